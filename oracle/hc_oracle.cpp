@@ -1,0 +1,392 @@
+// Oracle for the exact convolution of two D-dimensional hypercubes
+// (Serang, "An exact, cache-localized algorithm for the sub-quadratic
+// convolution of hypercubes", arXiv 1608.00206).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct
+// CPU statement of what the GPU library computes.  It shares no code, header,
+// table or helper with the CUDA path.  Only the test suite, the smoke check
+// and the benchmark's CPU-baseline leg may load it.
+//
+// Conventions (Introduction and Methods of the paper):
+//   x, y : hypercubes over {0,1}^D, row-major, flat length 2^D.  Axis 1 is the
+//          slowest axis: x[i_1] is the first or second half of the flat array.
+//   z    : the convolution over {0,1,2}^D, row-major, flat length 3^D.
+//          (x*y)[k] = sum over i+j=k of x[i]*y[j]   (definition, Introduction).
+// The int64 dtype computes in the ring Z/2^64 (uint64 arithmetic, wrap on
+// overflow); the paper says nothing about overflow and this is the reading
+// under which every order of operations gives the same bits.
+//
+// Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (never -Ofast):
+// floating-point results must follow the source's rounding order exactly.
+//
+// Parity pins for every function here live in tests/test_oracle_*.py.
+
+#include <cstdint>
+#include <cstddef>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <vector>
+#include <omp.h>
+
+namespace {
+
+typedef uint64_t u64;
+
+size_t pow3(int d) {
+  size_t r = 1;
+  for (int i = 0; i < d; ++i) r *= 3;
+  return r;
+}
+
+// t(i): the bits of i (axis 1 = most significant of D bits) read as base-3
+// digits (axis 1 = most significant digit).  Because every digit of
+// t(i)+t(j) is bit_d(i)+bit_d(j) <= 2, t(i)+t(j) is the flat index of the
+// multi-index sum i+j with no carries (Discussion: the carry-free example).
+size_t tmap(size_t i, int D) {
+  size_t r = 0;
+  for (int d = D - 1; d >= 0; --d) r = r * 3 + ((i >> d) & 1u);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (naive multidimensional convolution), specialised to hypercubes:
+// every pair (i, j) adds x[i]*y[j] into z[i+j].  O(4^D).
+template <class T>
+void brute(const T* x, const T* y, T* z, int D) {
+  const size_t n2 = (size_t)1 << D, n3 = pow3(D);
+  for (size_t k = 0; k < n3; ++k) z[k] = T(0);
+  std::vector<size_t> t(n2);
+  for (size_t i = 0; i < n2; ++i) t[i] = tmap(i, D);
+  for (size_t i = 0; i < n2; ++i)
+    for (size_t j = 0; j < n2; ++j) z[t[i] + t[j]] += x[i] * y[j];
+}
+
+// One output of the definition: z[k] = sum of x[i]*y[j] over the 2^{#ones(k)}
+// pairs with i+j = k.  Per axis, digit 0 forces (0,0), digit 2 forces (1,1),
+// digit 1 allows (0,1) and (1,0).  Pairs are visited in increasing i.
+template <class T>
+T point(const T* x, const T* y, int D, size_t k) {
+  int dig[64];
+  size_t kk = k;
+  for (int d = D - 1; d >= 0; --d) { dig[d] = (int)(kk % 3); kk /= 3; }
+  // dig[0] is axis 1 (most significant).
+  int ones[64], m = 0;
+  size_t ibase = 0;
+  for (int d = 0; d < D; ++d) {
+    size_t bit = (size_t)1 << (D - 1 - d);
+    if (dig[d] == 2) ibase |= bit;
+    if (dig[d] == 1) ones[m++] = d;
+  }
+  size_t jbase = ibase;
+  T acc = T(0);
+  for (size_t s = 0; s < ((size_t)1 << m); ++s) {
+    size_t i = ibase, j = jbase;
+    for (int q = 0; q < m; ++q) {
+      size_t bit = (size_t)1 << (D - 1 - ones[q]);
+      if ((s >> (m - 1 - q)) & 1u) i |= bit; else j |= bit;
+    }
+    acc += x[i] * y[j];
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// The Methods recurrence (3-way split), on fresh temporaries:
+//   z[0] = x[0]*y[0];  z[2] = x[1]*y[1];
+//   t    = (x[0]+x[1]) * (y[0]+y[1]);
+//   z[1] = (t - z[0]) - z[2];
+// with base case D = 0: z = x*y (the product of two numbers).  With
+// `direct` set, D = 1 is the base case instead, computed from the three
+// products of the 4-way form (z[1] = x[1]*y[0] + x[0]*y[1]).
+// The paper's in-place listing mutates x and y inside the first recursive
+// call, which the later x[0]+x[1] then reads; here the sums go to scratch and
+// x, y stay untouched.  `scratch` holds at least 2^(D+1) elements.
+template <class T>
+void rec(const T* x, const T* y, T* z, int D, bool direct, T* scratch) {
+  if (D == 0) {
+    z[0] = x[0] * y[0];
+    return;
+  }
+  if (D == 1 && direct) {
+    z[0] = x[0] * y[0];
+    z[1] = x[1] * y[0] + x[0] * y[1];
+    z[2] = x[1] * y[1];
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  rec(x, y, z, D - 1, direct, scratch);                  // z[0] = x[0]*y[0]
+  rec(x + h, y + h, z + 2 * n, D - 1, direct, scratch);  // z[2] = x[1]*y[1]
+  T* xs = scratch;
+  T* ys = scratch + h;
+  for (size_t k = 0; k < h; ++k) {
+    xs[k] = x[k] + x[h + k];
+    ys[k] = y[k] + y[h + k];
+  }
+  rec(xs, ys, z + n, D - 1, direct, scratch + 2 * h);    // t
+  for (size_t k = 0; k < n; ++k) z[n + k] = (z[n + k] - z[k]) - z[2 * n + k];
+}
+
+// Same recurrence with the three sub-problems of the top `par_levels` levels
+// run as OpenMP tasks.  Every element sees the same operations in the same
+// order as rec(), so the result is bitwise identical.
+template <class T>
+void rec_par(const T* x, const T* y, T* z, int D, bool direct, int par_levels) {
+  if (par_levels <= 0 || D <= 2) {
+    std::vector<T> scratch(((size_t)2 << D) + 2);
+    rec(x, y, z, D, direct, scratch.data());
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  std::vector<T> xs(h), ys(h);
+  for (size_t k = 0; k < h; ++k) {
+    xs[k] = x[k] + x[h + k];
+    ys[k] = y[k] + y[h + k];
+  }
+#pragma omp task shared(x, y, z)
+  rec_par(x, y, z, D - 1, direct, par_levels - 1);
+#pragma omp task shared(x, y, z)
+  rec_par(x + h, y + h, z + 2 * n, D - 1, direct, par_levels - 1);
+#pragma omp task shared(xs, ys, z)
+  rec_par(xs.data(), ys.data(), z + n, D - 1, direct, par_levels - 1);
+#pragma omp taskwait
+  for (size_t k = 0; k < n; ++k) z[n + k] = (z[n + k] - z[k]) - z[2 * n + k];
+}
+
+template <class T>
+void rec_top(const T* x, const T* y, T* z, int D, bool direct, int threads) {
+  if (threads <= 1) {
+    std::vector<T> scratch(((size_t)2 << D) + 2);
+    rec(x, y, z, D, direct, scratch.data());
+    return;
+  }
+  int levels = 0;
+  for (size_t w = 1; w < (size_t)threads * 3 && levels < D; w *= 3) ++levels;
+#pragma omp parallel num_threads(threads)
+#pragma omp single
+  rec_par(x, y, z, D, direct, levels);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision form: evaluation (x[0]+x[1]) and the product in binary32;
+// the cancelling interpolation (t - z[0]) - z[2] in float-float (a pair of
+// binary32 values carried through error-free two-sum), rounded to binary32
+// once at the end.  The float-float subtraction is
+//   (s, e) = two_sum(a.h, -b.h);  e = e + (a.l - b.l);  (h, l) = quick_two_sum(s, e)
+// with two_sum(a, b): s = a + b; v = s - a; e = (a - (s - v)) + (b - v)   (Knuth)
+// and quick_two_sum(a, b): s = a + b; e = b - (s - a)                      (Dekker).
+struct ff {
+  float h, l;
+};
+
+inline ff ff_sub(ff a, ff b) {
+  float s = a.h - b.h;
+  float v = s - a.h;
+  float e = (a.h - (s - v)) + (-b.h - v);
+  e = e + (a.l - b.l);
+  float h = s + e;
+  float l = e - (h - s);
+  return ff{h, l};
+}
+
+void rec_mixed(const float* x, const float* y, ff* z, int D, float* scratch) {
+  if (D == 0) {
+    z[0] = ff{x[0] * y[0], 0.0f};
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  rec_mixed(x, y, z, D - 1, scratch);
+  rec_mixed(x + h, y + h, z + 2 * n, D - 1, scratch);
+  float* xs = scratch;
+  float* ys = scratch + h;
+  for (size_t k = 0; k < h; ++k) {
+    xs[k] = x[k] + x[h + k];
+    ys[k] = y[k] + y[h + k];
+  }
+  rec_mixed(xs, ys, z + n, D - 1, scratch + 2 * h);
+  for (size_t k = 0; k < n; ++k) z[n + k] = ff_sub(ff_sub(z[n + k], z[k]), z[2 * n + k]);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (differentiation form).  For z = x*y and an upstream gradient g =
+// dL/dz, dL/dx[i] = sum_j g[i+j] * y[j] (a correlation).  Splitting axis 1 as
+// in the Methods section gives four correlations of dimension D-1,
+//   dx[0] = corr(g[0], y[0]) + corr(g[1], y[1])
+//   dx[1] = corr(g[1], y[0]) + corr(g[2], y[1]),
+// and bilinearity turns them into three:
+//   A = corr(g[0] - g[1], y[0]);  B = corr(g[2] - g[1], y[1]);
+//   C = corr(g[1], y[0] + y[1]);  dx[0] = A + C;  dx[1] = B + C.
+// This is the transpose of the forward recurrence, factor by factor.
+// `scratch` holds at least 3^D + 2^(D+1) elements.
+template <class T>
+void adj(const T* g, const T* w, T* out, int D, T* scratch) {
+  if (D == 0) {
+    out[0] = g[0] * w[0];
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  T* ga = scratch;          // g[0] - g[1]
+  T* gb = scratch + n;      // g[2] - g[1]
+  T* ws = scratch + 2 * n;  // w[0] + w[1]
+  T* c = ws + h;            // C
+  T* rest = c + h;
+  for (size_t k = 0; k < n; ++k) {
+    ga[k] = g[k] - g[n + k];
+    gb[k] = g[2 * n + k] - g[n + k];
+  }
+  for (size_t k = 0; k < h; ++k) ws[k] = w[k] + w[h + k];
+  adj(ga, w, out, D - 1, rest);           // A -> out[0..h)
+  adj(gb, w + h, out + h, D - 1, rest);   // B -> out[h..2h)
+  adj(g + n, ws, c, D - 1, rest);         // C
+  for (size_t k = 0; k < h; ++k) {
+    out[k] = out[k] + c[k];
+    out[h + k] = out[h + k] + c[k];
+  }
+}
+
+template <class T>
+size_t adj_scratch(int D) {
+  return pow3(D) + ((size_t)2 << D) + 8;
+}
+
+// Brute-force adjoint straight from the definition: dx[i] = sum_j g[t(i)+t(j)] y[j],
+// dy[j] = sum_i g[t(i)+t(j)] x[i].  O(4^D).
+template <class T>
+void adj_brute(const T* g, const T* x, const T* y, T* dx, T* dy, int D) {
+  const size_t n2 = (size_t)1 << D;
+  std::vector<size_t> t(n2);
+  for (size_t i = 0; i < n2; ++i) t[i] = tmap(i, D);
+  for (size_t i = 0; i < n2; ++i) {
+    T acc = T(0);
+    for (size_t j = 0; j < n2; ++j) acc += g[t[i] + t[j]] * y[j];
+    dx[i] = acc;
+  }
+  for (size_t j = 0; j < n2; ++j) {
+    T acc = T(0);
+    for (size_t i = 0; i < n2; ++i) acc += g[t[i] + t[j]] * x[i];
+    dy[j] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Companion magnitude for the floating-point forward-error bound: the same
+// recurrence on |x|, |y| with every subtraction turned into an addition,
+//   zabs[1] = t + zabs[0] + zabs[2].
+// Each output of the recurrence is reached through at most D additions per
+// operand, one product and 2D subtractions, so in precision u
+// |z_computed - z_exact| <= gamma_{3D+1} * zabs with gamma_n = n u / (1 - n u).
+void zabs_rec(const double* x, const double* y, double* z, int D, double* scratch) {
+  if (D == 0) {
+    z[0] = x[0] * y[0];
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  zabs_rec(x, y, z, D - 1, scratch);
+  zabs_rec(x + h, y + h, z + 2 * n, D - 1, scratch);
+  double* xs = scratch;
+  double* ys = scratch + h;
+  for (size_t k = 0; k < h; ++k) {
+    xs[k] = x[k] + x[h + k];
+    ys[k] = y[k] + y[h + k];
+  }
+  zabs_rec(xs, ys, z + n, D - 1, scratch + 2 * h);
+  for (size_t k = 0; k < n; ++k) z[n + k] = (z[n + k] + z[k]) + z[2 * n + k];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C entry points.  dtype codes: 0 = int64 (computed as uint64, wraps),
+// 1 = float64, 2 = float32.  All buffers are host memory owned by the caller.
+
+extern "C" {
+
+int oracle_brute(const void* x, const void* y, void* z, int D, int dtype) {
+  switch (dtype) {
+    case 0: brute((const u64*)x, (const u64*)y, (u64*)z, D); return 0;
+    case 1: brute((const double*)x, (const double*)y, (double*)z, D); return 0;
+    case 2: brute((const float*)x, (const float*)y, (float*)z, D); return 0;
+  }
+  return 1;
+}
+
+int oracle_points(const void* x, const void* y, int D, int dtype, const uint64_t* ks,
+                  size_t nk, void* out) {
+  for (size_t q = 0; q < nk; ++q) {
+    switch (dtype) {
+      case 0: ((u64*)out)[q] = point((const u64*)x, (const u64*)y, D, ks[q]); break;
+      case 1: ((double*)out)[q] = point((const double*)x, (const double*)y, D, ks[q]); break;
+      case 2: ((float*)out)[q] = point((const float*)x, (const float*)y, D, ks[q]); break;
+      default: return 1;
+    }
+  }
+  return 0;
+}
+
+int oracle_recurrence(const void* x, const void* y, void* z, int D, int dtype, int direct,
+                      int threads) {
+  switch (dtype) {
+    case 0: rec_top((const u64*)x, (const u64*)y, (u64*)z, D, direct != 0, threads); return 0;
+    case 1: rec_top((const double*)x, (const double*)y, (double*)z, D, direct != 0, threads); return 0;
+    case 2: rec_top((const float*)x, (const float*)y, (float*)z, D, direct != 0, threads); return 0;
+  }
+  return 1;
+}
+
+int oracle_recurrence_mixed(const float* x, const float* y, float* z, int D) {
+  std::vector<ff> w(pow3(D));
+  std::vector<float> scratch(((size_t)2 << D) + 2);
+  rec_mixed(x, y, w.data(), D, scratch.data());
+  for (size_t k = 0; k < w.size(); ++k) z[k] = w[k].h + w[k].l;
+  return 0;
+}
+
+int oracle_adjoint(const void* g, const void* x, const void* y, void* dx, void* dy, int D,
+                   int dtype) {
+  switch (dtype) {
+    case 0: {
+      std::vector<u64> s(adj_scratch<u64>(D));
+      if (dx) adj((const u64*)g, (const u64*)y, (u64*)dx, D, s.data());
+      if (dy) adj((const u64*)g, (const u64*)x, (u64*)dy, D, s.data());
+      return 0;
+    }
+    case 1: {
+      std::vector<double> s(adj_scratch<double>(D));
+      if (dx) adj((const double*)g, (const double*)y, (double*)dx, D, s.data());
+      if (dy) adj((const double*)g, (const double*)x, (double*)dy, D, s.data());
+      return 0;
+    }
+    case 2: {
+      std::vector<float> s(adj_scratch<float>(D));
+      if (dx) adj((const float*)g, (const float*)y, (float*)dx, D, s.data());
+      if (dy) adj((const float*)g, (const float*)x, (float*)dy, D, s.data());
+      return 0;
+    }
+  }
+  return 1;
+}
+
+int oracle_adjoint_brute(const void* g, const void* x, const void* y, void* dx, void* dy, int D,
+                         int dtype) {
+  switch (dtype) {
+    case 0: adj_brute((const u64*)g, (const u64*)x, (const u64*)y, (u64*)dx, (u64*)dy, D); return 0;
+    case 1: adj_brute((const double*)g, (const double*)x, (const double*)y, (double*)dx, (double*)dy, D); return 0;
+    case 2: adj_brute((const float*)g, (const float*)x, (const float*)y, (float*)dx, (float*)dy, D); return 0;
+  }
+  return 1;
+}
+
+int oracle_zabs(const double* absx, const double* absy, double* z, int D) {
+  std::vector<double> scratch(((size_t)2 << D) + 2);
+  zabs_rec(absx, absy, z, D, scratch.data());
+  return 0;
+}
+
+int oracle_max_threads(void) { return omp_get_max_threads(); }
+
+}  // extern "C"
