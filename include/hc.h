@@ -1,0 +1,179 @@
+/*
+ * hc.h -- C ABI of libhc, exact convolution of D-dimensional hypercubes on
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Introduction of Serang, arXiv 1608.00206):
+ *     (x * y)[k] = sum over i + j = k of x[i] * y[j],
+ * for x, y over {0,1}^D and z = x * y over {0,1,2}^D.  It is computed with the
+ * Methods-section recurrence -- per axis, z[0] = x[0]*y[0], z[2] = x[1]*y[1],
+ * z[1] = ((x[0]+x[1])*(y[0]+y[1]) - z[0]) - z[2] -- in O(D 3^D) operations
+ * instead of the O(4^D) of Algorithm 1.
+ *
+ * Layout (Methods, "tensors are stored in row-major format"):
+ *   x, y : 2^D elements, row-major, axis 1 slowest (x[i_1] is the first or
+ *          second half of the flat array).
+ *   z    : 3^D elements, row-major, axis 1 slowest: digit k_d of axis d has
+ *          weight 3^(D-d).  The carry-free example of the Discussion --
+ *          bits (1,1,1) + (1,0,1) -> digits (2,1,2) -- is flat index 23.
+ *
+ * Arithmetic:
+ *   HC_INT64      int64 in and out, computed in Z/2^64 (two's-complement
+ *                 wrap).  Exact whenever the true result fits in int64; the
+ *                 paper calls the method exact when (a + b) - a = b.
+ *   HC_FP64       float64 in and out.
+ *   HC_FP32       float32 in and out.
+ *   HC_FP32_MIXED float32 in and out; evaluation (sums) and products in
+ *                 float32, the cancelling interpolation (t - z[0]) - z[2] in
+ *                 float-float (error-free two-sum), one rounding at the end.
+ *   For every floating-point dtype the library applies the per-axis
+ *   operations in the recurrence's own order (evaluation axis 1 first,
+ *   interpolation axis D first) with no fused multiply-add, so results are
+ *   bitwise identical to the recurrence evaluated sequentially in the same
+ *   precision.  The forward error of each output is bounded by
+ *   gamma_{3D+1} * zabs, zabs being the recurrence on |x|, |y| with every
+ *   subtraction turned into an addition.
+ *
+ * Conventions common to every call:
+ *   - All data pointers are DEVICE memory owned by the caller, 16-byte
+ *     aligned (HC_ERR_ALIGN otherwise).  The library allocates nothing.
+ *   - Inputs (x, y, dz) are const and never modified (unlike the paper's
+ *     in-place listing, whose caption warns that x and y are overwritten).
+ *   - Outputs are fully overwritten and must not overlap any input or the
+ *     workspace (HC_ERR_ALIAS).
+ *   - 0 <= D <= HC_MAX_D (HC_ERR_ARG otherwise).  D = 0 gives z[0] = x[0]*y[0].
+ *   - workspace: device memory of at least the queried size, 256-byte
+ *     aligned; NULL is allowed when the queried size is 0.  It holds
+ *     intermediates and a status word; its contents need no initialisation.
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream):
+ *     they validate arguments, enqueue kernels and return without a host
+ *     synchronisation.  HC_ERR_CUDA reports a launch failure;
+ *     hc_last_cuda_error() gives CUDA's message.
+ *   - Calls with different workspaces may run concurrently on different
+ *     streams.  Calls sharing a workspace must be stream-ordered.
+ */
+#ifndef HC_H_
+#define HC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so this header needs no CUDA header. */
+typedef struct CUstream_st* hc_stream_t;
+
+typedef enum {
+  HC_INT64 = 0,
+  HC_FP64 = 1,
+  HC_FP32 = 2,
+  HC_FP32_MIXED = 3
+} hc_dtype;
+
+typedef enum {
+  HC_OK = 0,
+  HC_ERR_ARG = 1,       /* bad D, NULL pointer, n < 0, unknown flag          */
+  HC_ERR_DTYPE = 2,     /* unknown or unsupported dtype for this call        */
+  HC_ERR_ALIGN = 3,     /* pointer not 16-byte (workspace: 256-byte) aligned */
+  HC_ERR_ALIAS = 4,     /* an output overlaps an input or the workspace      */
+  HC_ERR_WORKSPACE = 5, /* workspace smaller than the queried size           */
+  HC_ERR_CUDA = 6,      /* a CUDA call failed; see hc_last_cuda_error()      */
+  HC_ERR_TIMEOUT = 7    /* a bounded device-side wait gave up (batched form) */
+} hc_status;
+
+#define HC_MAX_D 24
+
+/* Library version, (major << 16) | (minor << 8) | patch. */
+int hc_version(void);
+
+const char* hc_status_string(hc_status s);
+
+/* CUDA's message for the most recent HC_ERR_CUDA on the calling thread. */
+const char* hc_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------
+ * Plain form.
+ *
+ * hc_workspace_size: bytes of workspace hc_convolve needs for (D, dtype);
+ * returns 0 for an invalid (D, dtype) as well as when none is needed.
+ *
+ * hc_convolve: z = x * y.  x, y: 2^D elements; z: 3^D elements; all of the
+ * dtype's element type (int64, double or float; float for HC_FP32_MIXED).
+ */
+size_t hc_workspace_size(int D, hc_dtype dtype);
+
+hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dtype,
+                      void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+/* Explicit schedule (used by the autotuner and the tests; same result bits as
+ * hc_convolve for every valid schedule):
+ *   c    : innermost axes fused into one shared-memory tile, 1..9 for HC_FP32,
+ *          1..8 otherwise (clamped to D); 0 selects the default.
+ *   kmax : most outer axes interpolated per whole-array pass, 1..6; 0 = 6.
+ * HC_ERR_ARG for values out of range. */
+size_t hc_workspace_size_config(int D, hc_dtype dtype, int c, int kmax);
+
+hc_status hc_convolve_config(const void* x, const void* y, void* z, int D, hc_dtype dtype,
+                             int c, int kmax, void* workspace, size_t ws_bytes,
+                             hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Differentiation form.  For z = x * y and an upstream gradient dz = dL/dz
+ * (3^D elements):
+ *     dx[i] = sum_j dz[i + j] * y[j],     dy[j] = sum_i dz[i + j] * x[i],
+ * computed as the transpose of the recurrence, dx = E^T (I^T dz (.) E y),
+ * with per-axis I^T: (g0, g1, g2) -> (g0 - g1, g1, g2 - g1) and
+ * E^T: (h0, h1, h2) -> (h0 + h1, h1 + h2).  The evaluated operands E x and
+ * E y are recomputed tile by tile, never stored.  Either dx or dy may be
+ * NULL to skip it.  HC_FP32_MIXED is not supported here (HC_ERR_DTYPE).
+ */
+size_t hc_backward_workspace_size(int D, hc_dtype dtype);
+
+hc_status hc_convolve_backward(const void* dz, const void* x, const void* y, void* dx,
+                               void* dy, int D, hc_dtype dtype, void* workspace,
+                               size_t ws_bytes, hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batching form: n independent convolutions of possibly different D, one
+ * persistent kernel launch.  The instance array is HOST memory; its device
+ * pointers follow the plain-form rules, and no output may overlap another
+ * instance's buffers (not checked across instances).
+ *
+ * hc_convolve_batched = hc_batched_prepare + hc_batched_launch.
+ * hc_batched_prepare builds the work list on the host and copies it into the
+ * workspace (stream-ordered; the host array may be reused on return).
+ * hc_batched_launch only resets counters and launches, so it can be captured
+ * in a CUDA graph and replayed; every replay recomputes the prepared batch.
+ * Device-side waits are bounded: a wait that gives up records HC_ERR_TIMEOUT
+ * in the workspace status word (read it with hc_device_status).
+ */
+typedef struct {
+  const void* x;
+  const void* y;
+  void* z;
+  int D;
+} hc_instance;
+
+size_t hc_batched_workspace_size(const hc_instance* inst, int n, hc_dtype dtype);
+
+hc_status hc_convolve_batched(const hc_instance* inst, int n, hc_dtype dtype, void* workspace,
+                              size_t ws_bytes, hc_stream_t stream);
+
+hc_status hc_batched_prepare(const hc_instance* inst, int n, hc_dtype dtype, void* workspace,
+                             size_t ws_bytes, hc_stream_t stream);
+
+hc_status hc_batched_launch(void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Status word kept in the first bytes of every workspace.  Synchronises
+ * `stream`, then returns HC_OK or the error a kernel recorded there
+ * (HC_ERR_TIMEOUT).  HC_ERR_ARG for a NULL workspace.
+ */
+hc_status hc_device_status(const void* workspace, hc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HC_H_ */

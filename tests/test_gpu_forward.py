@@ -1,0 +1,221 @@
+"""GPU parity of the forward convolution (hc_convolve through the C ABI)
+against the CPU oracle.  Floating-point results must be bitwise identical to
+the oracle's recurrence in the same precision (same per-element operation
+order, no FMA); int64 results bitwise identical to Algorithm 1."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1608_00206_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def hc():
+    from paper_1608_00206_gb300.build import build
+    build()
+    import paper_1608_00206_gb300 as hc
+    assert torch.cuda.is_available()
+    return hc
+
+
+def gpu_conv(hc, x, y, **kw):
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    yt = torch.from_numpy(np.ascontiguousarray(y)).to(DEV)
+    z = hc.convolve(xt, yt, **kw)
+    torch.cuda.synchronize()
+    return z.cpu().numpy().reshape(-1)
+
+
+def bits(a):
+    return a.view(np.uint64) if a.dtype.itemsize == 8 else a.view(np.uint32)
+
+
+def assert_bit_equal(got, want):
+    assert got.shape == want.shape and got.dtype == want.dtype
+    bad = np.flatnonzero(bits(got) != bits(want))
+    assert bad.size == 0, f"{bad.size} mismatches, first at {bad[:5]}: {got[bad[:5]]} vs {want[bad[:5]]}"
+
+
+# ----------------------------------------------------------------- int64
+
+
+@pytest.mark.parametrize("D", list(range(0, 13)))
+def test_int64_bit_exact(hc, D):
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=100 + D)
+    want = oracle.brute_force(x, y) if D <= 10 else oracle.convolve(x, y, threads=8)
+    assert_bit_equal(gpu_conv(hc, x, y), want)
+
+
+@pytest.mark.parametrize("c", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("kmax", [1, 3, 4, 6])
+def test_int64_every_schedule(hc, c, kmax):
+    """Every (tile axes, axes per pass) schedule gives the same bits: D = 11
+    spans several tiles, K1/K3 passes of every width and ragged column tiles."""
+    D = 11
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=c * 10 + kmax)
+    assert_bit_equal(gpu_conv(hc, x, y, c=c, kmax=kmax), oracle.convolve(x, y))
+
+
+def test_int64_wraps(hc):
+    g = np.random.default_rng(3)
+    x = g.integers(-(1 << 62), 1 << 62, size=1 << 12, dtype=np.int64)
+    y = g.integers(-(1 << 62), 1 << 62, size=1 << 12, dtype=np.int64)
+    with np.errstate(over="ignore"):
+        assert_bit_equal(gpu_conv(hc, x, y), oracle.convolve(x, y))
+
+
+# --------------------------------------------------------- floating point
+
+
+@pytest.mark.parametrize("D", list(range(0, 14)))
+def test_fp64_bit_exact(hc, D):
+    x, y = inputs.prob_exponential_pair(D, seed=200 + D)
+    assert_bit_equal(gpu_conv(hc, x, y), oracle.convolve(x, y, threads=8))
+
+
+@pytest.mark.parametrize("D", list(range(0, 14)))
+def test_fp32_bit_exact(hc, D):
+    x, y = inputs.normal_pair(D, seed=300 + D)
+    assert_bit_equal(gpu_conv(hc, x, y), oracle.convolve(x, y, threads=8))
+
+
+@pytest.mark.parametrize("D", list(range(0, 14)))
+def test_mixed_bit_exact(hc, D):
+    x, y = inputs.uniform01_pair(D, seed=400 + D)
+    assert_bit_equal(gpu_conv(hc, x, y, mixed=True), oracle.convolve_mixed(x, y))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("c,kmax", [(1, 1), (4, 2), (7, 5), (8, 6), (9, 6)])
+def test_fp_every_schedule(hc, dt, c, kmax):
+    if c == 9 and dt != np.float32:
+        pytest.skip("9-axis tiles are float32 only")
+    D = 12
+    x, y = inputs.normal_pair(D, seed=c + kmax, dtype=dt)
+    assert_bit_equal(gpu_conv(hc, x, y, c=c, kmax=kmax), oracle.convolve(x, y, threads=8))
+
+
+def test_mixed_every_schedule(hc):
+    D = 12
+    x, y = inputs.uniform01_pair(D, seed=5)
+    want = oracle.convolve_mixed(x, y)
+    for c, kmax in [(2, 1), (5, 4), (8, 6)]:
+        assert_bit_equal(gpu_conv(hc, x, y, mixed=True, c=c, kmax=kmax), want)
+
+
+def test_paper_accuracy_workload(hc):
+    """Table 1 input x = y = [1..2^D]: z[0...0] = 1 exactly, z[2...2] = 4^D."""
+    for D in (11, 14, 16):
+        x = inputs.paper_accuracy(D)
+        z = gpu_conv(hc, x, x)
+        assert z[0] == 1.0 and z[-1] == float(4 ** D)
+
+
+# ------------------------------------------------------------ full sizes
+
+
+def test_d16_fp64_probability_full(hc):
+    """D = 16 float64 PMFs (Exponential(1) normalised): all 3^16 outputs bitwise
+    equal to the oracle recurrence; the sum is 1."""
+    x, y = inputs.prob_exponential_pair(16, seed=16)
+    z = gpu_conv(hc, x, y)
+    assert_bit_equal(z, oracle.convolve(x, y, threads=16))
+    assert abs(z.sum() - 1.0) < 1e-12
+
+
+def test_d16_fp64_separable_closed_form(hc):
+    D = 16
+    x, y, a, b = inputs.prob_separable_pair(D, seed=7)
+    c = np.stack([a[:, 0] * b[:, 0], a[:, 0] * b[:, 1] + a[:, 1] * b[:, 0], a[:, 1] * b[:, 1]], 1)
+    z_closed = inputs.outer_product_cube(c)
+    z = gpu_conv(hc, x, y)
+    za = oracle.zabs(x, y)
+    u = 2.0 ** -53
+    bound = oracle.gamma(3 * D + 1, u) * za + oracle.gamma(3 * D, u) * np.abs(z_closed)
+    assert np.all(np.abs(z - z_closed) <= bound)
+
+
+def test_d20_int64_full_size(hc):
+    """D = 20 int64, values in [-1000, 1000] (the benchmark workload, same
+    launch configuration): 3^20 outputs, 27.9 GB.  Checked on whole slices
+    (prefix digits fixed, the oracle's 16-D recurrence on the matching
+    sub-cubes), on random single outputs (the definition), and on the sum
+    invariant over all outputs."""
+    D = 20
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2020)
+    xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
+    z = hc.convolve(xt, yt)
+    torch.cuda.synchronize()
+    # sum invariant (no overflow: |sum z| <= (2^20 * 1000)^2)
+    assert int(z.sum().item()) == int(x.sum()) * int(y.sum())
+    # slices with 4 leading digits fixed: digit 0 -> (0, 0), 2 -> (1, 1)
+    n16 = 3 ** 16
+    for digits in [(0, 0, 0, 0), (2, 2, 2, 2), (0, 2, 2, 0)]:
+        off_z = sum(d * 3 ** (3 - i) for i, d in enumerate(digits)) * n16
+        sel = sum((d // 2) << (3 - i) for i, d in enumerate(digits)) << 16
+        want = oracle.convolve(x[sel:sel + (1 << 16)], y[sel:sel + (1 << 16)], threads=16)
+        got = z[off_z:off_z + n16].cpu().numpy()
+        assert np.array_equal(got, want), digits
+    g = np.random.default_rng(0)
+    ks = np.sort(g.integers(0, 3 ** D, size=20000, dtype=np.int64))
+    got = z[torch.from_numpy(ks).to(DEV)].cpu().numpy()
+    assert np.array_equal(got, oracle.points(x, y, ks))
+    del z
+
+
+def test_d20_int64_separable_points(hc):
+    D = 20
+    a = inputs.separable_factors(D, 1, "int")
+    b = inputs.separable_factors(D, 2, "int")
+    x, y = inputs.outer_product_cube(a), inputs.outer_product_cube(b)
+    z = hc.convolve(torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV))
+    g = np.random.default_rng(1)
+    ks = g.integers(0, 3 ** D, size=5000, dtype=np.int64)
+    got = z[torch.from_numpy(ks).to(DEV)].cpu().numpy()
+    c = np.stack([a[:, 0] * b[:, 0], a[:, 0] * b[:, 1] + a[:, 1] * b[:, 0], a[:, 1] * b[:, 1]], 1)
+    want = np.ones(ks.size, np.int64)
+    kk = ks.copy()
+    with np.errstate(over="ignore"):
+        for d in range(D - 1, -1, -1):
+            want = want * c[d][kk % 3]
+            kk //= 3
+    assert np.array_equal(got, want)
+    del z
+
+
+# ------------------------------------------------------------ host buffers
+
+
+def test_host_buffers_end_to_end(hc):
+    D = 13
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=13)
+    xt = torch.from_numpy(x).pin_memory()
+    yt = torch.from_numpy(y).pin_memory()
+    z = hc.convolve(xt, yt)
+    assert not z.is_cuda and z.is_pinned()
+    assert np.array_equal(z.numpy(), oracle.convolve(x, y))
+
+
+def test_shaped_input_gives_shaped_output(hc):
+    x = torch.arange(1, 9, dtype=torch.float64, device=DEV).reshape(2, 2, 2)
+    z = hc.convolve(x, x)
+    assert z.shape == (3, 3, 3)
+    assert z[2, 1, 2].item() == float(oracle.convolve(x.cpu().numpy(), x.cpu().numpy())[23])
+
+
+def test_stream_ordering(hc):
+    """The call is asynchronous on the given stream."""
+    D = 14
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
+        z = hc.convolve(xt, yt)
+        zc = z.cpu()
+    assert np.array_equal(zc.numpy(), oracle.convolve(x, y))
