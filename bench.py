@@ -1,0 +1,577 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 hypercube convolution (arXiv 1608.00206).
+
+Metric: 3^D outputs per second (whole job, all ranks), with the dominant
+kernel's achieved HBM bandwidth against the measured peak.  One step is one
+pass of the whole method over the workload's inputs, which are resident in
+HBM before the timed region starts.
+
+Workloads (--workload):
+  d20_int64  (default) D = 20 int64 exact, x, y iid uniform integers in
+             [-1000, 1000]; z has 3^20 = 3.49e9 int64 outputs (27.9 GB)
+  d16_fp64   D = 16 float64 probability hypercubes (Exponential(1) / sum)
+  d16_mixed  the same inputs in float32, float-float interpolation
+  d10_int64  D = 10 int64, values in [-100, 100]
+  batched    4096 float32 instances, D ~ U{6..14}, U[0,1) inputs, one
+             persistent launch replayed from a CUDA graph
+  fwdbwd     D = 18 float32, x, y, w iid N(0,1), loss = sum(w * z), forward
+             plus the hand-written adjoint through torch.autograd
+
+--impl reference times the CPU oracle (the plain C++ recurrence, all host
+cores) on bounded samples of the same workload and prints the same JSON line
+with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3^D outputs/s"
+UNIT = "outputs/s"
+
+WORKLOADS = {
+    "d20_int64": "D=20 int64 exact single instance: x,y 2^20 iid uniform integers in "
+                 "[-1000,1000]; z 3^20 int64 (27.9 GB)",
+    "d16_fp64": "D=16 float64 probability hypercubes: x,y 2^16 iid Exponential(1) normalised "
+                "to sum 1; z 3^16 float64",
+    "d16_mixed": "D=16 float32 probability hypercubes, float32 evaluation and products, "
+                 "float-float interpolation",
+    "d10_int64": "D=10 int64 exact: x,y 1024 iid uniform integers in [-100,100]",
+    "batched": "4096 float32 instances, D iid uniform in 6..14, x,y iid U[0,1); one persistent "
+               "launch replayed from a CUDA graph",
+    "fwdbwd": "D=18 float32, x,y,w iid N(0,1), loss = sum(w*z), forward + hand-written adjoint "
+              "via torch.autograd",
+}
+DEFAULT_STEPS = {"d20_int64": 30, "d16_fp64": 30, "d16_mixed": 50, "d10_int64": 200,
+                 "batched": 20, "fwdbwd": 30}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 throughput of GB300 from the nominal dense FP64 rate (1.25 TFLOP/s,
+# counting a fused multiply-add as two): 0.625e12 FP64 add, subtract or
+# multiply instructions per second.
+FP64_OPS_PEAK = 0.625e12
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1608_00206_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def _traffic_from_profiles(workload, kernel):
+    """dram bytes per launch from profiles/traffic.txt when captured on the
+    current kernel sources (same source hash); None otherwise."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = _src_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#"):
+                if parts[0] == workload and parts[1] == kernel and parts[3] == src:
+                    return float(parts[2])
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.out = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            self.sel = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.sel:
+                cmd += ["-i", self.sel]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workloads
+
+
+class Workload:
+    """Device-resident inputs, a step function and the bookkeeping for one
+    workload."""
+
+    def __init__(self, name, dev, rank=0):
+        import numpy as np
+        import torch
+
+        import paper_1608_00206_gb300 as hc
+        from paper_1608_00206_gb300 import inputs
+
+        self.name = name
+        self.dev = dev
+        self.hc = hc
+        self.torch = torch
+        seed = 1000 + rank
+        self.graph = None
+        if name in ("d20_int64", "d10_int64"):
+            D = 20 if name == "d20_int64" else 10
+            r = 1000 if D == 20 else 100
+            x, y = inputs.uniform_int_pair(D, -r, r, seed)
+            self._single(D, x, y, torch.int64, mixed=False)
+            self.dtype = "int64"
+        elif name in ("d16_fp64", "d16_mixed"):
+            D = 16
+            x, y = inputs.prob_exponential_pair(D, seed)
+            if name == "d16_mixed":
+                x, y = x.astype(np.float32), y.astype(np.float32)
+            self._single(D, x, y, torch.float64 if name == "d16_fp64" else torch.float32,
+                         mixed=(name == "d16_mixed"))
+            self.dtype = "f64" if name == "d16_fp64" else "f32+ff"
+        elif name == "batched":
+            dims = inputs.batched_dims(4096, 6, 14, seed)
+            pairs = inputs.batched_uniform01(dims, seed + 1)
+            self.dims = [int(d) for d in dims]
+            self.host_pairs = pairs
+            self.xs = [torch.from_numpy(x).to(dev) for x, _ in pairs]
+            self.ys = [torch.from_numpy(y).to(dev) for _, y in pairs]
+            self.batch = hc.BatchedConv(self.xs, self.ys)
+            self.batch.capture()
+            self.outputs = sum(3 ** d for d in self.dims)
+            self.alg_bytes = sum(4 * (3 ** d + 2 * 2 ** d) for d in self.dims)
+            self.dtype = "f32"
+            self.D = None
+        elif name == "fwdbwd":
+            D = 18
+            self.D = D
+            x = inputs.normal(1 << D, seed, np.float32)
+            y = inputs.normal(1 << D, seed + 1, np.float32)
+            w = inputs.normal(3 ** D, seed + 2, np.float32)
+            self.host = (x, y, w)
+            self.x = torch.from_numpy(x).to(dev).requires_grad_()
+            self.y = torch.from_numpy(y).to(dev).requires_grad_()
+            self.w = torch.from_numpy(w).to(dev)
+            self.outputs = 3 ** D
+            # forward writes z (3^D), backward reads dz (3^D); inputs and grads 2^D each
+            self.alg_bytes = 4 * (2 * 3 ** D + 4 * 2 ** D)
+            self.dtype = "f32"
+        else:
+            raise ValueError(name)
+
+    def _single(self, D, x, y, tdtype, mixed):
+        torch = self.torch
+        self.D = D
+        self.mixed = mixed
+        self.host = (x, y)
+        self.x = torch.from_numpy(x).to(self.dev)
+        self.y = torch.from_numpy(y).to(self.dev)
+        self.z = torch.empty(3 ** D, dtype=tdtype, device=self.dev)
+        nb = self.hc.workspace_size(D, tdtype, mixed)
+        self.ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=self.dev)
+        self.outputs = 3 ** D
+        s = x.itemsize
+        self.alg_bytes = 3 ** D * s + 2 * 2 ** D * s
+
+    def step(self):
+        if self.name == "batched":
+            self.batch.replay()
+        elif self.name == "fwdbwd":
+            self.x.grad = None
+            self.y.grad = None
+            loss = (self.w * self.hc.hypercube_conv(self.x, self.y)).sum()
+            loss.backward()
+        else:
+            self.hc.convolve(self.x, self.y, out=self.z, mixed=self.mixed, workspace=self.ws)
+
+    # per-kernel algorithmic bytes (or FP64 operations) per launch
+    def kernel_alg(self, kname, launches_per_step):
+        D = self.D
+        if self.name == "batched":
+            return self.alg_bytes, "hbm"
+        s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64") else 4
+        sw = 8 if self.name == "d16_mixed" else s
+        if self.name == "d16_fp64":
+            return self._fp64_ops(kname, launches_per_step), "alu"
+        if kname in ("interp_pass", "interp_t_pass"):
+            return 2 * 3 ** D * sw, "hbm"  # read and write the whole 3^D array
+        if kname in ("tile_conv", "tile_adj"):
+            C = min(D, 9 if (s == 4 and self.name != "d16_mixed" and kname == "tile_conv") else 8)
+            a = D - C
+            return 3 ** D * sw + 2 * 3 ** a * 2 ** C * s, "hbm"
+        return None, "hbm"
+
+    def _fp64_ops(self, kname, lps):
+        D = self.D
+        C = min(D, 8)
+        a = D - C
+        if kname == "tile_conv":
+            # per tile: evaluation of both operands on C axes, 3^C products,
+            # interpolation of C axes (2 subtractions per 3 outputs per axis)
+            per_tile = 2 * (3 ** C - 2 ** C) + 3 ** C + 2 * C * 3 ** (C - 1)
+            return 3 ** a * per_tile
+        if kname == "interp_pass":
+            k = a / max(1, lps)
+            return 2 * k * 3 ** (D - 1)
+        return None
+
+
+def _time_steps(wl, steps, warmup, dist):
+    import torch
+
+    from paper_1608_00206_gb300 import _lib
+
+    for _ in range(warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    _lib.profile_collect()  # drop anything recorded so far
+    _lib.lib().hc_profile_enable(1)
+    clocks = ClockSampler(wl.dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed region
+    stream = torch.cuda.current_stream(wl.dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        wl.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _lib.lib().hc_profile_enable(0)
+    clk = clocks.stop()
+    prof = _lib.profile_collect()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=wl.dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    return ms, prof, clk
+
+
+def _e2e(wl, steps=3, warmup=1):
+    """Same metric through the public API with host (pinned) buffers: every
+    step copies x, y to the device, convolves, and copies z back."""
+    import torch
+
+    hc = wl.hc
+    if wl.name in ("batched", "fwdbwd"):
+        return _e2e_other(wl, steps, warmup)
+    x, y = wl.host
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    zh = torch.empty(3 ** wl.D, dtype=xh.dtype, pin_memory=True)
+    # the device-resident output is not needed here
+    wl.z = None
+    torch.cuda.empty_cache()
+    for _ in range(warmup):
+        hc.convolve(xh, yh, out=zh, mixed=wl.mixed, workspace=wl.ws)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        hc.convolve(xh, yh, out=zh, mixed=wl.mixed, workspace=wl.ws)
+    dt = time.perf_counter() - t0
+    return {"value": wl.outputs * steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(2 * x.nbytes), "d2h_bytes_per_step": int(zh.numel() * zh.element_size())}
+
+
+def _e2e_other(wl, steps, warmup):
+    import torch
+
+    hc = wl.hc
+    if wl.name == "batched":
+        xh = [torch.from_numpy(x).pin_memory() for x, _ in wl.host_pairs]
+        yh = [torch.from_numpy(y).pin_memory() for _, y in wl.host_pairs]
+        zh = [torch.empty(3 ** d, dtype=torch.float32, pin_memory=True) for d in wl.dims]
+        h2d = sum(x.nbytes * 2 for x, _ in wl.host_pairs)
+        d2h = sum(4 * 3 ** d for d in wl.dims)
+
+        def one():
+            for i in range(len(xh)):
+                wl.xs[i].copy_(xh[i], non_blocking=True)
+                wl.ys[i].copy_(yh[i], non_blocking=True)
+            wl.batch.replay()
+            for i in range(len(zh)):
+                zh[i].copy_(wl.batch.outs[i].view(-1), non_blocking=True)
+            torch.cuda.synchronize()
+    else:
+        x, y, w = wl.host
+        xh, yh, wh = (torch.from_numpy(a).pin_memory() for a in (x, y, w))
+        gxh = torch.empty_like(xh).pin_memory()
+        gyh = torch.empty_like(yh).pin_memory()
+        h2d = x.nbytes + y.nbytes + w.nbytes
+        d2h = x.nbytes + y.nbytes + 4
+
+        def one():
+            xd = xh.to(wl.dev, non_blocking=True).requires_grad_()
+            yd = yh.to(wl.dev, non_blocking=True).requires_grad_()
+            wd = wh.to(wl.dev, non_blocking=True)
+            loss = (wd * hc.hypercube_conv(xd, yd)).sum()
+            loss.backward()
+            gxh.copy_(xd.grad, non_blocking=True)
+            gyh.copy_(yd.grad, non_blocking=True)
+            loss.item()
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = time.perf_counter() - t0
+    return {"value": wl.outputs * steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+
+def _oracle_samples(name):
+    """Bounded samples of the workload for the CPU oracle: a list of
+    (description, callable returning the number of outputs computed)."""
+    import numpy as np
+
+    import oracle
+    from paper_1608_00206_gb300 import inputs
+
+    thr = os.cpu_count() or 1
+    seed = 1000
+    if name == "d20_int64":
+        x, y = inputs.uniform_int_pair(20, -1000, 1000, seed)
+        samples = []
+        for d1 in (0, 2):
+            for d2 in (0, 2):
+                sel = ((d1 // 2) * 2 + (d2 // 2)) << 18
+                xs, ys = x[sel:sel + (1 << 18)].copy(), y[sel:sel + (1 << 18)].copy()
+                samples.append((lambda xs=xs, ys=ys: oracle.convolve(xs, ys, threads=thr).size))
+        return ("slices z[d1,d2,:] (d1,d2 in {0,2}) of the D=20 problem: the 18-D recurrence on "
+                "the matching sub-cubes, 3^18 outputs each", samples, thr)
+    if name in ("d16_fp64", "d16_mixed"):
+        x, y = inputs.prob_exponential_pair(16, seed)
+        if name == "d16_mixed":
+            x32, y32 = x.astype(np.float32), y.astype(np.float32)
+            f = lambda: oracle.convolve_mixed(x32, y32).size  # noqa: E731
+            return "the full D=16 problem (single thread)", [f], 1
+        return "the full D=16 problem", [lambda: oracle.convolve(x, y, threads=thr).size], thr
+    if name == "d10_int64":
+        x, y = inputs.uniform_int_pair(10, -100, 100, seed)
+        return "the full D=10 problem (single thread)", [lambda: oracle.convolve(x, y).size], 1
+    if name == "batched":
+        dims = inputs.batched_dims(4096, 6, 14, seed)
+        pairs = inputs.batched_uniform01(dims, seed + 1)
+        samples = []
+        for lo in range(0, 4096, 256):
+            chunk = pairs[lo:lo + 256]
+            samples.append(lambda chunk=chunk: sum(oracle.convolve(a, b, threads=thr).size
+                                                   for a, b in chunk))
+        return "consecutive blocks of 256 of the 4096 instances", samples, thr
+    if name == "fwdbwd":
+        D = 18
+        x = inputs.normal(1 << D, seed, np.float32)
+        y = inputs.normal(1 << D, seed + 1, np.float32)
+        w = inputs.normal(3 ** D, seed + 2, np.float32)
+
+        def f():
+            z = oracle.convolve(x, y, threads=thr)
+            oracle.adjoint(w, x, y)
+            return z.size
+        return "the full D=18 forward (all cores) and adjoint (single thread)", [f], thr
+    raise ValueError(name)
+
+
+def _cpu_baseline(name, budget_s=12.0):
+    desc, samples, thr = _oracle_samples(name)
+    outs, t = 0, 0.0
+    i = 0
+    while i < len(samples) and (t < budget_s or i == 0):
+        t0 = time.perf_counter()
+        outs += samples[i]()
+        t += time.perf_counter() - t0
+        i += 1
+    return {"value": outs / t, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{i} of: {desc}; {t:.1f} s"}
+
+
+def _reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    desc, samples, thr = _oracle_samples(args.workload)
+    for i in range(args.warmup):
+        samples[i % len(samples)]()
+    outs, t = 0, 0.0
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        outs += samples[i % len(samples)]()
+        t += time.perf_counter() - t0
+    v = outs / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": _dtype_name(args.workload), "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _dtype_name(w):
+    return {"d20_int64": "int64", "d10_int64": "int64", "d16_fp64": "f64", "d16_mixed": "f32+ff",
+            "batched": "f32", "fwdbwd": "f32"}[w]
+
+
+# ------------------------------------------------------------------- main
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="d20_int64", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS[args.workload]
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return _reference_arm(args, rank, world)
+
+    import torch
+
+    from paper_1608_00206_gb300.build import build
+
+    if rank == 0 or world == 1:
+        build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+        if rank != 0:
+            build()  # the library is in-tree; the build is a no-op once rank 0 made it
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    wl = Workload(args.workload, dev, rank)
+    ms, prof, clk = _time_steps(wl, args.steps, args.warmup, dist)
+    value = world * wl.outputs * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peak_hbm, peak_kind = _peaks()
+    roof = None
+    if prof:
+        kname, (launches, kms) = max(prof.items(), key=lambda kv: kv[1][1])
+        lps = launches / args.steps
+        alg, bound = wl.kernel_alg(kname, lps)
+        per_launch_ms = kms / launches
+        if alg is not None:
+            if bound == "alu":
+                achieved = alg / (per_launch_ms / 1e3) / 1e12
+                roof = {"bound": "alu", "kernel": kname, "achieved": achieved,
+                        "peak": FP64_OPS_PEAK / 1e12, "unit": "TFLOP/s",
+                        "frac": achieved / (FP64_OPS_PEAK / 1e12), "traffic": None,
+                        "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2)"}
+            else:
+                achieved = alg / (per_launch_ms / 1e3) / 1e9
+                roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_hbm,
+                        "unit": "GB/s", "frac": achieved / peak_hbm,
+                        "traffic": _traffic_from_profiles(args.workload, kname),
+                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    launches = sum(v[0] for v in prof.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": _dtype_name(args.workload),
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                   "outputs_per_step": wl.outputs, "parallelism": f"replicas{world}",
+                   "l2": "working set larger than L2 (129 MB); no flush"
+                   if args.workload in ("d20_int64", "d16_fp64", "d16_mixed", "batched", "fwdbwd")
+                   else "L2 flushed: no (working set below L2)"},
+        "roofline": roof,
+        "alg_hbm_frac": (wl.alg_bytes * args.steps / (ms / 1e3) / 1e9) / peak_hbm,
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_e2e:
+        line["e2e"] = _e2e(wl)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

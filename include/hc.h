@@ -140,9 +140,14 @@ hc_status hc_convolve_backward(const void* dz, const void* x, const void* y, voi
  * pointers follow the plain-form rules, and no output may overlap another
  * instance's buffers (not checked across instances).
  *
+ * Each instance has 0 <= D <= 14 (15 for HC_FP32): the tile axes plus at
+ * most six outer axes (HC_ERR_ARG otherwise; larger D go to hc_convolve).
+ *
  * hc_convolve_batched = hc_batched_prepare + hc_batched_launch.
- * hc_batched_prepare builds the work list on the host and copies it into the
- * workspace (stream-ordered; the host array may be reused on return).
+ * hc_batched_prepare builds the work list on the host, copies it into the
+ * workspace and synchronises `stream` (so it cannot be captured; the host
+ * array may be reused on return).  It remembers the plan under the workspace
+ * address for later launches.
  * hc_batched_launch only resets counters and launches, so it can be captured
  * in a CUDA graph and replayed; every replay recomputes the prepared batch.
  * Device-side waits are bounded: a wait that gives up records HC_ERR_TIMEOUT
@@ -164,6 +169,32 @@ hc_status hc_batched_prepare(const hc_instance* inst, int n, hc_dtype dtype, voi
                              size_t ws_bytes, hc_stream_t stream);
 
 hc_status hc_batched_launch(void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+/* Testing aid for the bounded waits (failure detection without a GPU fault):
+ * rewrites the prepared work list in `workspace` so that the interpolation
+ * tickets of `instance` wait for one more finished tile than the instance
+ * has.  The next hc_batched_launch then records HC_ERR_TIMEOUT in the status
+ * word after about a second, skips those tickets (their outputs are left
+ * incomplete) and finishes every other instance.  hc_batched_prepare undoes
+ * it.  Synchronous.  HC_ERR_ARG if the workspace was not prepared or the
+ * instance is out of range.  Instances with D <= the tile axes (8; 9 for
+ * HC_FP32) have no waits, so the call has no effect on them. */
+hc_status hc_batched_inject_stall(void* workspace, int instance);
+
+/* ------------------------------------------------------------------------
+ * Tracing.  hc_profile_enable(1) makes every later kernel launch of the
+ * library (any thread, any stream) record a pair of CUDA events on its own
+ * stream around the kernel; hc_profile_enable(0) stops recording.
+ * hc_profile_collect waits for the recorded events, then writes per kernel
+ * name (NUL-terminated, name_len bytes per entry, in `names`) the number of
+ * launches and their total device time in milliseconds, for at most
+ * max_kernels names, clears the records and returns the number of names
+ * written.  Any output array may be NULL.  Tracing adds two event records per
+ * launch and is off by default. */
+hc_status hc_profile_enable(int on);
+
+int hc_profile_collect(char* names, int name_len, double* total_ms, int* counts,
+                       int max_kernels);
 
 /* ------------------------------------------------------------------------
  * Status word kept in the first bytes of every workspace.  Synchronises

@@ -37,7 +37,11 @@ SIGNATURES = {
     "hc_convolve_batched": (_i, [ctypes.POINTER(hc_instance), _i, _i, _vp, _sz, _vp]),
     "hc_batched_prepare": (_i, [ctypes.POINTER(hc_instance), _i, _i, _vp, _sz, _vp]),
     "hc_batched_launch": (_i, [_vp, _sz, _vp]),
+    "hc_batched_inject_stall": (_i, [_vp, _i]),
     "hc_device_status": (_i, [_vp, _vp]),
+    "hc_profile_enable": (_i, [_i]),
+    "hc_profile_collect": (_i, [_cp, _i, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int), _i]),
 }
 
 _LOCK = threading.Lock()
@@ -82,6 +86,16 @@ def missing_symbols():
 def check(status: int, what: str = "") -> None:
     if status != HC_OK:
         raise HCError(status, what)
+
+
+def profile_collect(max_kernels: int = 32):
+    """{kernel name: (launches, total device ms)} since the last collect."""
+    names = ctypes.create_string_buffer(64 * max_kernels)
+    ms = (ctypes.c_double * max_kernels)()
+    cnt = (ctypes.c_int * max_kernels)()
+    n = lib().hc_profile_collect(names, 64, ms, cnt, max_kernels)
+    return {names.raw[64 * i:64 * (i + 1)].split(b"\0")[0].decode(): (int(cnt[i]), float(ms[i]))
+            for i in range(n)}
 
 
 def __getattr__(name):

@@ -125,3 +125,133 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
     out.view(-1).copy_(zd, non_blocking=out.is_pinned())
     torch.cuda.current_stream(dev).synchronize()
     return out
+
+
+def convolve_backward(dz: torch.Tensor, x: torch.Tensor, y: torch.Tensor, *,
+                      need_dx: bool = True, need_dy: bool = True,
+                      workspace: torch.Tensor | None = None, stream=None):
+    """(dx, dy) for z = x * y and upstream gradient dz (3^D elements), by the
+    transposed recurrence; either may be skipped (returned as None)."""
+    D = dim_of(x)
+    code = _code(x.dtype, False)
+    if not (x.is_cuda and y.is_cuda and dz.is_cuda):
+        raise ValueError("convolve_backward takes CUDA tensors")
+    if dz.numel() != 3 ** D or dz.dtype != x.dtype or y.dtype != x.dtype or y.numel() != x.numel():
+        raise ValueError("dz must have 3^D elements and all dtypes must match")
+    if not (need_dx or need_dy):
+        return None, None
+    dz, x, y = dz.contiguous(), x.contiguous(), y.contiguous()
+    dx = torch.empty_like(x) if need_dx else None
+    dy = torch.empty_like(y) if need_dy else None
+    lib = _lib.lib()
+    nbytes = int(lib.hc_backward_workspace_size(D, code))
+    ws = _workspace(nbytes, x.device, workspace)
+    s = lib.hc_convolve_backward(_ptr(dz), _ptr(x), _ptr(y), _ptr(dx), _ptr(dy), D, code,
+                                 _ptr(ws), nbytes, _stream(x.device, stream))
+    check(s, "hc_convolve_backward")
+    return dx, dy
+
+
+class HypercubeConv(torch.autograd.Function):
+    """z = x * y with the hand-written adjoint as its backward.  Only x and y
+    are saved; the evaluated operands are recomputed inside the backward
+    kernels."""
+
+    @staticmethod
+    def forward(ctx, x, y):
+        ctx.save_for_backward(x, y)
+        return convolve(x, y)
+
+    @staticmethod
+    def backward(ctx, gz):
+        x, y = ctx.saved_tensors
+        dx, dy = convolve_backward(gz.reshape(-1), x, y, need_dx=ctx.needs_input_grad[0],
+                                   need_dy=ctx.needs_input_grad[1])
+        return dx, dy
+
+
+def hypercube_conv(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """Differentiable z = x * y (float32 or float64 CUDA tensors)."""
+    return HypercubeConv.apply(x, y)
+
+
+class BatchedConv:
+    """A prepared batch of independent convolutions (the batching form).
+
+    ``xs``, ``ys``: sequences of CUDA tensors (2^D_i elements each, one dtype,
+    D_i <= 14, or 15 for float32).  The work list is built once
+    (hc_batched_prepare); :meth:`launch` runs the whole batch as one
+    persistent kernel and can be captured in a CUDA graph (:meth:`capture`),
+    whose replays recompute the batch from the current contents of xs, ys.
+    """
+
+    def __init__(self, xs, ys, outs=None, *, mixed: bool = False, stream=None):
+        if len(xs) != len(ys):
+            raise ValueError("xs and ys differ in length")
+        self.n = len(xs)
+        dtype = xs[0].dtype if self.n else torch.float32
+        self.code = _code(dtype, mixed)
+        self.device = xs[0].device if self.n else torch.device("cuda", torch.cuda.current_device())
+        self.xs = [x.contiguous() for x in xs]
+        self.ys = [y.contiguous() for y in ys]
+        self.dims = []
+        for x, y in zip(self.xs, self.ys):
+            if not (x.is_cuda and y.is_cuda) or x.dtype != dtype or y.dtype != dtype:
+                raise ValueError("batched inputs must be CUDA tensors of one dtype")
+            if x.numel() != y.numel():
+                raise ValueError("x and y of an instance differ in size")
+            self.dims.append(dim_of(x))
+        if outs is None:
+            outs = [torch.empty(_out_shape(x, D), dtype=dtype, device=self.device)
+                    for x, D in zip(self.xs, self.dims)]
+        self.outs = outs
+        arr = (_lib.hc_instance * max(1, self.n))()
+        for i, (x, y, z, D) in enumerate(zip(self.xs, self.ys, self.outs, self.dims)):
+            arr[i] = _lib.hc_instance(x.data_ptr(), y.data_ptr(), z.data_ptr(), D)
+        self._arr = arr
+        lib = _lib.lib()
+        self.ws_bytes = int(lib.hc_batched_workspace_size(arr, self.n, self.code))
+        if self.n and self.ws_bytes == 0:
+            raise ValueError("batch rejected (an instance has D out of range or bad buffers)")
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8,
+                                     device=self.device)
+        check(lib.hc_batched_prepare(arr, self.n, self.code, self.workspace.data_ptr(),
+                                     self.ws_bytes, _stream(self.device, stream)),
+              "hc_batched_prepare")
+        self.graph = None
+
+    def launch(self, stream=None):
+        check(_lib.lib().hc_batched_launch(self.workspace.data_ptr(), self.ws_bytes,
+                                           _stream(self.device, stream)), "hc_batched_launch")
+        return self.outs
+
+    def capture(self):
+        """Capture one launch in a CUDA graph (after one eager warm-up launch)."""
+        self.launch()
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self.launch()
+        self.graph = g
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+        return self.outs
+
+    def status(self) -> int:
+        """Synchronises and returns the workspace status word (0 = HC_OK)."""
+        return int(_lib.lib().hc_device_status(self.workspace.data_ptr(),
+                                               _stream(self.device, None)))
+
+    def inject_stall(self, instance: int):
+        check(_lib.lib().hc_batched_inject_stall(self.workspace.data_ptr(), instance),
+              "hc_batched_inject_stall")
+
+
+def convolve_batched(xs, ys, outs=None, *, mixed: bool = False, stream=None):
+    """One persistent launch over all instances; returns the list of outputs."""
+    b = BatchedConv(xs, ys, outs, mixed=mixed, stream=stream)
+    return b.launch(stream)

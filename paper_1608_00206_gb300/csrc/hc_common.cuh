@@ -24,6 +24,12 @@ typedef unsigned long long u64;
 __host__ __device__ constexpr int p3(int k) { return k <= 0 ? 1 : 3 * p3(k - 1); }
 __host__ __device__ constexpr int p2(int k) { return 1 << k; }
 
+__host__ __device__ inline long long pow3_dev(int k) {
+  long long r = 1;
+  for (int i = 0; i < k; ++i) r *= 3;
+  return r;
+}
+
 inline size_t pow3z(int k) {
   size_t r = 1;
   for (int i = 0; i < k; ++i) r *= 3;

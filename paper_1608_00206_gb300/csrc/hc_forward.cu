@@ -19,44 +19,21 @@
 #include <mutex>
 
 #include "hc_common.cuh"
+#include "hc_profile.cuh"
 #include "hc_forward.cuh"
 #include "hc_kernels.cuh"
+#include "hc_tile.cuh"
+#include <type_traits>
 
 namespace hc {
 
 // ---------------------------------------------------------------------------
-// K2: the fused tile.  C inner axes, split into G = ceil(C/3) groups of at
-// most 3 axes (the outermost group takes the remainder).  Per tile alpha:
-//   stage 0      : global Xo[alpha], Yo[alpha] -> evaluate group 0 -> smem
-//   stage 1      : (G = 3) evaluate group 1 in smem
-//   fused stage  : evaluate the innermost group, multiply, interpolate the
-//                  innermost group, all in registers -> W tile in smem
-//   interp stages: interpolate group G-2 .. 1 in smem, then group 0 from smem
-//                  straight to global memory
-// Every stage gives consecutive threads consecutive innermost indices, so
-// shared-memory accesses are bank-conflict free (odd strides) and global
-// accesses are contiguous per warp.  The buffer feeding the fused stage is
-// stored transposed ([2^g][3^(C-g)]) so that its pencils, which are
-// contiguous in the natural layout, are read with unit stride across threads.
-template <int C>
-struct TileShape {
-  static constexpr int G = (C + 2) / 3;
-  static constexpr int g0 = C - 3 * (G - 1);          // outermost group
-  static constexpr int gL = (G == 1) ? C : 3;         // innermost group
-  static constexpr int nLastPencils = p3(C - gL);     // pencils of the fused stage
-};
-
-template <class M, int C>
-struct TileSmem {
-  typedef typename M::In In;
-  typedef typename M::W W;
-  // W tile; the stage-0 buffer of a 3-group tile lives inside it.
-  static constexpr size_t kW = sizeof(W) * (size_t)p3(C);
-  // transposed buffer feeding the fused stage, per operand
-  static constexpr size_t kLast = sizeof(In) * (size_t)p2(TileShape<C>::gL) * p3(C - TileShape<C>::gL);
-  static constexpr size_t kS1 = TileShape<C>::G == 3 ? 2 * sizeof(In) * (size_t)p3(TileShape<C>::g0) * p2(C - TileShape<C>::g0) : 0;
-  static_assert(kS1 <= kW, "stage-0 buffer must fit inside the W tile");
-  static constexpr size_t bytes = kW + (TileShape<C>::G >= 2 ? 2 * kLast : 0);
+// K2 kernel: one tile per outer index alpha (grid-stride over tiles).
+template <class In>
+struct RowLoader {
+  const In* x;
+  const In* y;
+  __device__ __forceinline__ In operator()(int op, int i) const { return op ? y[i] : x[i]; }
 };
 
 template <class M, int C, bool FINAL>
@@ -64,150 +41,12 @@ __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __
                                                         const typename M::In* __restrict__ Y,
                                                         void* __restrict__ out_, long long ntiles) {
   typedef typename M::In In;
-  typedef typename M::W W;
-  typedef typename M::Out Out;
-  typedef TileShape<C> S;
+  typedef typename std::conditional<FINAL, typename M::Out, typename M::W>::type O;
   extern __shared__ __align__(16) unsigned char smem[];
-  W* Ws = reinterpret_cast<W*>(smem);
-  In* LastX = reinterpret_cast<In*>(smem + TileSmem<M, C>::kW);
-  In* LastY = LastX + p2(S::gL) * p3(C - S::gL);
-  In* S1 = reinterpret_cast<In*>(smem);  // G == 3 only; aliases the W tile
-  const int tid = threadIdx.x;
-  const int nt = blockDim.x;
-
 #pragma unroll 1
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const In* xr = X + t * p2(C);
-    const In* yr = Y + t * p2(C);
-    if constexpr (S::G == 1) {
-      // C <= 3: one pencil, straight from global to global.
-      if (tid == 0) {
-        In a[p3(C)], b[p3(C)];
-#pragma unroll
-        for (int i = 0; i < p2(C); ++i) {
-          a[i] = xr[i];
-          b[i] = yr[i];
-        }
-        eval_pencil<M, C>(a);
-        eval_pencil<M, C>(b);
-        W w[p3(C)];
-#pragma unroll
-        for (int j = 0; j < p3(C); ++j) w[j] = M::mul(a[j], b[j]);
-        interp_pencil<M, C>(w);
-        if constexpr (FINAL) {
-          Out* o = reinterpret_cast<Out*>(out_) + t * p3(C);
-#pragma unroll
-          for (int j = 0; j < p3(C); ++j) o[j] = M::out(w[j]);
-        } else {
-          W* o = reinterpret_cast<W*>(out_) + t * p3(C);
-#pragma unroll
-          for (int j = 0; j < p3(C); ++j) o[j] = w[j];
-        }
-      }
-    } else {
-      // ---- stage 0: evaluate group 0 (g0 axes) from global memory.
-      {
-        constexpr int R = p2(C - S::g0);  // pencils per operand
-        #pragma unroll 1
-        for (int p = tid; p < 2 * R; p += nt) {
-          const int op = p / R, r = p - op * R;
-          const In* src = op ? yr : xr;
-          In v[p3(S::g0)];
-#pragma unroll
-          for (int b = 0; b < p2(S::g0); ++b) v[b] = src[b * R + r];
-          eval_pencil<M, S::g0>(v);
-          if constexpr (S::G == 2) {
-            // next is the fused stage: transposed [2^gL][3^g0], r = last-group bits
-            In* d = op ? LastY : LastX;
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) d[r * p3(S::g0) + j] = v[j];
-          } else {
-            In* d = S1 + op * (p3(S::g0) * R);
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) d[j * R + r] = v[j];
-          }
-        }
-      }
-      __syncthreads();
-      // ---- stage 1 (G == 3): evaluate group 1 (3 axes) in shared memory.
-      if constexpr (S::G == 3) {
-        constexpr int O = p3(S::g0);
-        constexpr int R = p2(S::gL);  // remaining binary axes (innermost group)
-        constexpr int NP = O * R;
-        #pragma unroll 1
-        for (int p = tid; p < 2 * NP; p += nt) {
-          const int op = p / NP, q = p - op * NP;
-          const int o = q / R, r = q - o * R;
-          const In* s = S1 + op * (O * 8 * R);
-          In v[27];
-#pragma unroll
-          for (int b = 0; b < 8; ++b) v[b] = s[(o * 8 + b) * R + r];
-          eval_pencil<M, 3>(v);
-          In* d = op ? LastY : LastX;
-#pragma unroll
-          for (int j = 0; j < 27; ++j) d[r * (O * 27) + o * 27 + j] = v[j];
-        }
-        __syncthreads();
-      }
-      // ---- fused stage: evaluate innermost group, multiply, interpolate it.
-      {
-        constexpr int NO = S::nLastPencils;
-        #pragma unroll 1
-        for (int o = tid; o < NO; o += nt) {
-          In a[27], b[27];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            a[q] = LastX[q * NO + o];
-            b[q] = LastY[q * NO + o];
-          }
-          eval_pencil<M, 3>(a);
-          eval_pencil<M, 3>(b);
-          W w[27];
-#pragma unroll
-          for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
-          interp_pencil<M, 3>(w);
-#pragma unroll
-          for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
-        }
-      }
-      __syncthreads();
-      // ---- interpolate group 1 (G == 3) in shared memory.
-      if constexpr (S::G == 3) {
-        constexpr int O = p3(S::g0), R = 27;
-        #pragma unroll 1
-        for (int p = tid; p < O * R; p += nt) {
-          const int o = p / R, r = p - o * R;
-          W v[27];
-#pragma unroll
-          for (int j = 0; j < 27; ++j) v[j] = Ws[(o * 27 + j) * R + r];
-          interp_pencil<M, 3>(v);
-#pragma unroll
-          for (int j = 0; j < 27; ++j) Ws[(o * 27 + j) * R + r] = v[j];
-        }
-        __syncthreads();
-      }
-      // ---- interpolate group 0 and write the tile to global memory.
-      {
-        constexpr int R = p3(C - S::g0);
-        #pragma unroll 1
-        for (int r = tid; r < R; r += nt) {
-          W v[p3(S::g0)];
-#pragma unroll
-          for (int j = 0; j < p3(S::g0); ++j) v[j] = Ws[j * R + r];
-          interp_pencil<M, S::g0>(v);
-          if constexpr (FINAL) {
-            Out* o = reinterpret_cast<Out*>(out_) + t * p3(C);
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = M::out(v[j]);
-          } else {
-            W* o = reinterpret_cast<W*>(out_) + t * p3(C);
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = v[j];
-          }
-        }
-      }
-      __syncthreads();  // the next tile reuses shared memory
-    }
+    RowLoader<In> ld{X + t * p2(C), Y + t * p2(C)};
+    tile_body<M, C, FINAL>(ld, reinterpret_cast<O*>(out_) + t * p3(C), smem);
   }
 }
 
@@ -219,85 +58,22 @@ __global__ void scalar_conv_kernel(const typename M::In* x, const typename M::In
 }
 
 // ---------------------------------------------------------------------------
-// K3: interpolate k = K1 + K2 consecutive axes of a [hi][3^k][lo] array.
-// A CTA tile is all 3^k rows of L consecutive columns of one h.  Round 1
-// interpolates the inner K2 axes in registers (pencils read straight from
-// global memory, stride lo), round 2 the outer K1 axes after a pass through
-// shared memory.  Consecutive threads take consecutive columns.  src and dst
-// may be the same array (in place) -- every tile reads all its elements
-// before writing any, and tiles are disjoint.
+// K3 kernel: interpolate k = K1 + K2 consecutive axes of a [hi][3^k][lo]
+// array; a CTA tile is all 3^k rows of L consecutive columns of one h.
+// src and dst may be the same array (every tile reads its elements before
+// writing any; tiles are disjoint).
 template <class M, int K1, int K2, int L, bool FINAL>
 __global__ void __launch_bounds__(256) interp_pass_kernel(const typename M::W* src, void* dst_,
                                                           long long hi, long long lo) {
-  typedef typename M::W W;
-  typedef typename M::Out Out;
-  constexpr int K = K1 + K2;
-  constexpr int ROWS = p3(K);
   extern __shared__ __align__(16) unsigned char smem[];
-  W* T = reinterpret_cast<W*>(smem);
   const long long ctiles = (lo + L - 1) / L;
   const long long ntiles = hi * ctiles;
-  const int tid = threadIdx.x, nt = blockDim.x;
-
 #pragma unroll 1
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long h = tile / ctiles;
     const long long l0 = (tile - h * ctiles) * L;
-    const long long base = h * ROWS * lo + l0;
-    if constexpr (K1 == 0) {
-#pragma unroll 1
-      for (int l = tid; l < L; l += nt) {
-        if (l0 + l >= lo) continue;
-        W v[p3(K2)];
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) v[j] = src[base + j * lo + l];
-        interp_pencil<M, K2>(v);
-        if constexpr (FINAL) {
-          Out* d = reinterpret_cast<Out*>(dst_);
-#pragma unroll
-          for (int j = 0; j < p3(K2); ++j) d[base + j * lo + l] = M::out(v[j]);
-        } else {
-          W* d = reinterpret_cast<W*>(dst_);
-#pragma unroll
-          for (int j = 0; j < p3(K2); ++j) d[base + j * lo + l] = v[j];
-        }
-      }
-    } else {
-      // round 1: inner K2 axes, global -> registers -> shared
-      #pragma unroll 1
-      for (int p = tid; p < p3(K1) * L; p += nt) {
-        const int o = p / L, l = p - o * L;
-        if (l0 + l >= lo) continue;
-        W v[p3(K2)];
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) v[j] = src[base + (long long)(o * p3(K2) + j) * lo + l];
-        interp_pencil<M, K2>(v);
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) T[(o * p3(K2) + j) * L + l] = v[j];
-      }
-      __syncthreads();
-      // round 2: outer K1 axes, shared -> registers -> global
-      #pragma unroll 1
-      for (int p = tid; p < p3(K2) * L; p += nt) {
-        const int r = p / L, l = p - r * L;
-        if (l0 + l >= lo) continue;
-        W v[p3(K1)];
-#pragma unroll
-        for (int j = 0; j < p3(K1); ++j) v[j] = T[(j * p3(K2) + r) * L + l];
-        interp_pencil<M, K1>(v);
-        if constexpr (FINAL) {
-          Out* d = reinterpret_cast<Out*>(dst_);
-#pragma unroll
-          for (int j = 0; j < p3(K1); ++j)
-            d[base + (long long)(j * p3(K2) + r) * lo + l] = M::out(v[j]);
-        } else {
-          W* d = reinterpret_cast<W*>(dst_);
-#pragma unroll
-          for (int j = 0; j < p3(K1); ++j) d[base + (long long)(j * p3(K2) + r) * lo + l] = v[j];
-        }
-      }
-      __syncthreads();  // shared tile reused by the next tile
-    }
+    interp_tile_body<M, K1, K2, L, FINAL, false>(src, dst_, h * p3(K1 + K2) * lo + l0, l0, lo,
+                                                 smem);
   }
 }
 
@@ -321,6 +97,7 @@ static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* 
                                  long long ntiles, cudaStream_t st) {
   const size_t smem = TileSmem<M, C>::bytes;
   auto k = tile_conv_kernel<M, C, FINAL>;
+  ProfileScope prof(st, "tile_conv");
   cudaError_t e = prep_kernel(k, smem);
   if (e != cudaSuccess) return e;
   const int threads = threads_for_tile(C);
@@ -353,6 +130,7 @@ static cudaError_t launch_interp_k(const typename M::W* src, void* dst, long lon
   constexpr int L = ColsPerTile<M>::L;
   const size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
   auto k = interp_pass_kernel<M, K1, K2, L, FINAL>;
+  ProfileScope prof(st, "interp_pass");
   cudaError_t e = prep_kernel(k, smem);
   if (e != cudaSuccess) return e;
   int threads = K1 > 0 ? 256 : L;
@@ -444,6 +222,7 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
   typedef typename M::W W;
   const int D = p.D, C = p.C, a = p.a;
   if (D == 0) {
+    ProfileScope prof(st, "scalar_conv");
     scalar_conv_kernel<M><<<1, 32, 0, st>>>((const In*)x, (const In*)y, (typename M::Out*)z);
     return cudaGetLastError();
   }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "hc_common.cuh"
+#include "hc_profile.cuh"
 
 namespace hc {
 
@@ -58,6 +59,7 @@ template <class M, int K>
 inline cudaError_t launch_eval_k(const typename M::In* sx, const typename M::In* sy,
                                  typename M::In* dx, typename M::In* dy, long long hi, long long lo,
                                  cudaStream_t st) {
+  ProfileScope prof(st, "eval_pass");
   auto k = eval_pass_kernel<M, K>;
   const long long cols = hi * lo;
   long long blocks = (cols + 255) / 256;

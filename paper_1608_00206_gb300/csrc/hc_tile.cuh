@@ -1,0 +1,289 @@
+// Tile bodies shared by the plain kernels (one launch per pass) and the
+// persistent batched kernel.
+#pragma once
+
+#include "hc_common.cuh"
+
+namespace hc {
+
+template <bool CG, class T>
+__device__ __forceinline__ T ldw(const T* p) {
+  if constexpr (CG) {
+    if constexpr (sizeof(T) == 8) {
+      unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long*>(p));
+      T r;
+      memcpy(&r, &v, 8);
+      return r;
+    } else {
+      unsigned int v = __ldcg(reinterpret_cast<const unsigned int*>(p));
+      T r;
+      memcpy(&r, &v, 4);
+      return r;
+    }
+  } else {
+    return *p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: the fused tile.  C inner axes, split into G = ceil(C/3) groups of at
+// most 3 axes (the outermost group takes the remainder).  Per tile alpha:
+//   stage 0      : global Xo[alpha], Yo[alpha] -> evaluate group 0 -> smem
+//   stage 1      : (G = 3) evaluate group 1 in smem
+//   fused stage  : evaluate the innermost group, multiply, interpolate the
+//                  innermost group, all in registers -> W tile in smem
+//   interp stages: interpolate group G-2 .. 1 in smem, then group 0 from smem
+//                  straight to global memory
+// Every stage gives consecutive threads consecutive innermost indices, so
+// shared-memory accesses are bank-conflict free (odd strides) and global
+// accesses are contiguous per warp.  The buffer feeding the fused stage is
+// stored transposed ([2^g][3^(C-g)]) so that its pencils, which are
+// contiguous in the natural layout, are read with unit stride across threads.
+template <int C>
+struct TileShape {
+  static constexpr int G = (C + 2) / 3;
+  static constexpr int g0 = C - 3 * (G - 1);          // outermost group
+  static constexpr int gL = (G == 1) ? C : 3;         // innermost group
+  static constexpr int nLastPencils = p3(C - gL);     // pencils of the fused stage
+};
+
+template <class M, int C>
+struct TileSmem {
+  typedef typename M::In In;
+  typedef typename M::W W;
+  // W tile; the stage-0 buffer of a 3-group tile lives inside it.
+  static constexpr size_t kW = sizeof(W) * (size_t)p3(C);
+  // transposed buffer feeding the fused stage, per operand
+  static constexpr size_t kLast = sizeof(In) * (size_t)p2(TileShape<C>::gL) * p3(C - TileShape<C>::gL);
+  static constexpr size_t kS1 = TileShape<C>::G == 3 ? 2 * sizeof(In) * (size_t)p3(TileShape<C>::g0) * p2(C - TileShape<C>::g0) : 0;
+  static_assert(kS1 <= kW, "stage-0 buffer must fit inside the W tile");
+  static constexpr size_t bytes = kW + (TileShape<C>::G >= 2 ? 2 * kLast : 0);
+};
+
+// Loader: ld(op, i) returns element i of the tile's operand row (op 0 = x,
+// 1 = y), already evaluated on the outer axes.  out_tile: the tile's 3^C
+// outputs.  smem: TileSmem<M, C>::bytes of shared memory.
+template <class M, int C, bool FINAL, class Loader>
+__device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ out_tile,
+                                          unsigned char* smem) {
+  typedef typename M::In In;
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  typedef TileShape<C> S;
+  W* Ws = reinterpret_cast<W*>(smem);
+  In* LastX = reinterpret_cast<In*>(smem + TileSmem<M, C>::kW);
+  In* LastY = LastX + p2(S::gL) * p3(C - S::gL);
+  In* S1 = reinterpret_cast<In*>(smem);  // G == 3 only; aliases the W tile
+  const int tid = threadIdx.x;
+  const int nt = blockDim.x;
+
+  {
+    if constexpr (S::G == 1) {
+      // C <= 3: one pencil, straight from global to global.
+      if (tid == 0) {
+        In a[p3(C)], b[p3(C)];
+#pragma unroll
+        for (int i = 0; i < p2(C); ++i) {
+          a[i] = ld(0, i);
+          b[i] = ld(1, i);
+        }
+        eval_pencil<M, C>(a);
+        eval_pencil<M, C>(b);
+        W w[p3(C)];
+#pragma unroll
+        for (int j = 0; j < p3(C); ++j) w[j] = M::mul(a[j], b[j]);
+        interp_pencil<M, C>(w);
+        if constexpr (FINAL) {
+          Out* o = reinterpret_cast<Out*>(out_tile);
+#pragma unroll
+          for (int j = 0; j < p3(C); ++j) o[j] = M::out(w[j]);
+        } else {
+          W* o = reinterpret_cast<W*>(out_tile);
+#pragma unroll
+          for (int j = 0; j < p3(C); ++j) o[j] = w[j];
+        }
+      }
+    } else {
+      // ---- stage 0: evaluate group 0 (g0 axes) from global memory.
+      {
+        constexpr int R = p2(C - S::g0);  // pencils per operand
+        #pragma unroll 1
+        for (int p = tid; p < 2 * R; p += nt) {
+          const int op = p / R, r = p - op * R;
+          In v[p3(S::g0)];
+#pragma unroll
+          for (int b = 0; b < p2(S::g0); ++b) v[b] = ld(op, b * R + r);
+          eval_pencil<M, S::g0>(v);
+          if constexpr (S::G == 2) {
+            // next is the fused stage: transposed [2^gL][3^g0], r = last-group bits
+            In* d = op ? LastY : LastX;
+#pragma unroll
+            for (int j = 0; j < p3(S::g0); ++j) d[r * p3(S::g0) + j] = v[j];
+          } else {
+            In* d = S1 + op * (p3(S::g0) * R);
+#pragma unroll
+            for (int j = 0; j < p3(S::g0); ++j) d[j * R + r] = v[j];
+          }
+        }
+      }
+      __syncthreads();
+      // ---- stage 1 (G == 3): evaluate group 1 (3 axes) in shared memory.
+      if constexpr (S::G == 3) {
+        constexpr int O = p3(S::g0);
+        constexpr int R = p2(S::gL);  // remaining binary axes (innermost group)
+        constexpr int NP = O * R;
+        #pragma unroll 1
+        for (int p = tid; p < 2 * NP; p += nt) {
+          const int op = p / NP, q = p - op * NP;
+          const int o = q / R, r = q - o * R;
+          const In* s = S1 + op * (O * 8 * R);
+          In v[27];
+#pragma unroll
+          for (int b = 0; b < 8; ++b) v[b] = s[(o * 8 + b) * R + r];
+          eval_pencil<M, 3>(v);
+          In* d = op ? LastY : LastX;
+#pragma unroll
+          for (int j = 0; j < 27; ++j) d[r * (O * 27) + o * 27 + j] = v[j];
+        }
+        __syncthreads();
+      }
+      // ---- fused stage: evaluate innermost group, multiply, interpolate it.
+      {
+        constexpr int NO = S::nLastPencils;
+        #pragma unroll 1
+        for (int o = tid; o < NO; o += nt) {
+          In a[27], b[27];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            a[q] = LastX[q * NO + o];
+            b[q] = LastY[q * NO + o];
+          }
+          eval_pencil<M, 3>(a);
+          eval_pencil<M, 3>(b);
+          W w[27];
+#pragma unroll
+          for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
+          interp_pencil<M, 3>(w);
+#pragma unroll
+          for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
+        }
+      }
+      __syncthreads();
+      // ---- interpolate group 1 (G == 3) in shared memory.
+      if constexpr (S::G == 3) {
+        constexpr int O = p3(S::g0), R = 27;
+        #pragma unroll 1
+        for (int p = tid; p < O * R; p += nt) {
+          const int o = p / R, r = p - o * R;
+          W v[27];
+#pragma unroll
+          for (int j = 0; j < 27; ++j) v[j] = Ws[(o * 27 + j) * R + r];
+          interp_pencil<M, 3>(v);
+#pragma unroll
+          for (int j = 0; j < 27; ++j) Ws[(o * 27 + j) * R + r] = v[j];
+        }
+        __syncthreads();
+      }
+      // ---- interpolate group 0 and write the tile to global memory.
+      {
+        constexpr int R = p3(C - S::g0);
+        #pragma unroll 1
+        for (int r = tid; r < R; r += nt) {
+          W v[p3(S::g0)];
+#pragma unroll
+          for (int j = 0; j < p3(S::g0); ++j) v[j] = Ws[j * R + r];
+          interp_pencil<M, S::g0>(v);
+          if constexpr (FINAL) {
+            Out* o = reinterpret_cast<Out*>(out_tile);
+#pragma unroll
+            for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = M::out(v[j]);
+          } else {
+            W* o = reinterpret_cast<W*>(out_tile);
+#pragma unroll
+            for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = v[j];
+          }
+        }
+      }
+      __syncthreads();  // the caller's next tile reuses shared memory
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: interpolate k = K1 + K2 consecutive axes of a [hi][3^k][lo] array.
+// A CTA tile is all 3^k rows of L consecutive columns of one h.  Round 1
+// interpolates the inner K2 axes in registers (pencils read straight from
+// global memory, stride lo), round 2 the outer K1 axes after a pass through
+// shared memory.  Consecutive threads take consecutive columns.  src and dst
+// may be the same array (in place) -- every tile reads all its elements
+// before writing any, and tiles are disjoint.
+// One tile: rows base + j * lo for j < 3^k, columns l0 + [0, L) clipped to
+// lo (base already includes l0).  CG = read src through L2 only (data
+// written by other CTAs of the same launch).
+template <class M, int K1, int K2, int L, bool FINAL, bool CG>
+__device__ __forceinline__ void interp_tile_body(const typename M::W* src, void* dst_,
+                                                 long long base, long long l0, long long lo,
+                                                 unsigned char* smem) {
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  W* T = reinterpret_cast<W*>(smem);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  {
+    if constexpr (K1 == 0) {
+#pragma unroll 1
+      for (int l = tid; l < L; l += nt) {
+        if (l0 + l >= lo) continue;
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = ldw<CG>(src + base + j * lo + l);
+        interp_pencil<M, K2>(v);
+        if constexpr (FINAL) {
+          Out* d = reinterpret_cast<Out*>(dst_);
+#pragma unroll
+          for (int j = 0; j < p3(K2); ++j) d[base + j * lo + l] = M::out(v[j]);
+        } else {
+          W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+          for (int j = 0; j < p3(K2); ++j) d[base + j * lo + l] = v[j];
+        }
+      }
+    } else {
+      // round 1: inner K2 axes, global -> registers -> shared
+      #pragma unroll 1
+      for (int p = tid; p < p3(K1) * L; p += nt) {
+        const int o = p / L, l = p - o * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = ldw<CG>(src + base + (long long)(o * p3(K2) + j) * lo + l);
+        interp_pencil<M, K2>(v);
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) T[(o * p3(K2) + j) * L + l] = v[j];
+      }
+      __syncthreads();
+      // round 2: outer K1 axes, shared -> registers -> global
+      #pragma unroll 1
+      for (int p = tid; p < p3(K2) * L; p += nt) {
+        const int r = p / L, l = p - r * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K1)];
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) v[j] = T[(j * p3(K2) + r) * L + l];
+        interp_pencil<M, K1>(v);
+        if constexpr (FINAL) {
+          Out* d = reinterpret_cast<Out*>(dst_);
+#pragma unroll
+          for (int j = 0; j < p3(K1); ++j)
+            d[base + (long long)(j * p3(K2) + r) * lo + l] = M::out(v[j]);
+        } else {
+          W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+          for (int j = 0; j < p3(K1); ++j) d[base + (long long)(j * p3(K2) + r) * lo + l] = v[j];
+        }
+      }
+      __syncthreads();  // shared tile reused by the caller's next tile
+    }
+  }
+}
+
+}  // namespace hc
