@@ -47,13 +47,15 @@ WORKLOADS = {
     "d16_mixed": "D=16 float32 probability hypercubes, float32 evaluation and products, "
                  "float-float interpolation",
     "d10_int64": "D=10 int64 exact: x,y 1024 iid uniform integers in [-100,100]",
+    "d18_fp32": "D=18 float32: x,y 2^18 iid U[0,1); z 3^18 float32",
     "batched": "4096 float32 instances, D iid uniform in 6..14, x,y iid U[0,1); one persistent "
                "launch replayed from a CUDA graph",
     "fwdbwd": "D=18 float32, x,y,w iid N(0,1), loss = sum(w*z), forward + hand-written adjoint "
               "via torch.autograd",
 }
 DEFAULT_STEPS = {"d20_int64": 30, "d16_fp64": 30, "d16_mixed": 50, "d10_int64": 200,
-                 "batched": 20, "fwdbwd": 30}
+                 "d18_fp32": 50, "batched": 20, "fwdbwd": 30}
+SINGLE = ("d20_int64", "d16_fp64", "d16_mixed", "d10_int64", "d18_fp32")
 
 
 def _peaks():
@@ -161,7 +163,7 @@ class Workload:
     """Device-resident inputs, a step function and the bookkeeping for one
     workload."""
 
-    def __init__(self, name, dev, rank=0):
+    def __init__(self, name, dev, rank=0, D_override=None):
         import numpy as np
         import torch
 
@@ -175,13 +177,18 @@ class Workload:
         seed = 1000 + rank
         self.graph = None
         if name in ("d20_int64", "d10_int64"):
-            D = 20 if name == "d20_int64" else 10
-            r = 1000 if D == 20 else 100
+            D = D_override or (20 if name == "d20_int64" else 10)
+            r = 1000 if name == "d20_int64" else 100
             x, y = inputs.uniform_int_pair(D, -r, r, seed)
             self._single(D, x, y, torch.int64, mixed=False)
             self.dtype = "int64"
+        elif name == "d18_fp32":
+            D = D_override or 18
+            x, y = inputs.uniform01_pair(D, seed)
+            self._single(D, x, y, torch.float32, mixed=False)
+            self.dtype = "f32"
         elif name in ("d16_fp64", "d16_mixed"):
-            D = 16
+            D = D_override or 16
             x, y = inputs.prob_exponential_pair(D, seed)
             if name == "d16_mixed":
                 x, y = x.astype(np.float32), y.astype(np.float32)
@@ -294,15 +301,28 @@ def _time_steps(wl, steps, warmup, dist):
     stream = torch.cuda.current_stream(wl.dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    graph_events = []
     e0.record(stream)
     for _ in range(steps):
-        wl.step()
+        if wl.name == "batched":
+            # a graph replay is one batched kernel (plus two counter resets);
+            # the tracer does not see inside replays, so time each replay
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            wl.step()
+            b.record(stream)
+            graph_events.append((a, b))
+        else:
+            wl.step()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     _lib.lib().hc_profile_enable(0)
     clk = clocks.stop()
     prof = _lib.profile_collect()
+    if graph_events:
+        prof["batched"] = (len(graph_events), sum(a.elapsed_time(b) for a, b in graph_events))
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=wl.dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -413,6 +433,9 @@ def _oracle_samples(name):
             f = lambda: oracle.convolve_mixed(x32, y32).size  # noqa: E731
             return "the full D=16 problem (single thread)", [f], 1
         return "the full D=16 problem", [lambda: oracle.convolve(x, y, threads=thr).size], thr
+    if name == "d18_fp32":
+        x, y = inputs.uniform01_pair(18, seed)
+        return "the full D=18 problem", [lambda: oracle.convolve(x, y, threads=thr).size], thr
     if name == "d10_int64":
         x, y = inputs.uniform_int_pair(10, -100, 100, seed)
         return "the full D=10 problem (single thread)", [lambda: oracle.convolve(x, y).size], 1
@@ -478,7 +501,7 @@ def _reference_arm(args, rank, world):
 
 def _dtype_name(w):
     return {"d20_int64": "int64", "d10_int64": "int64", "d16_fp64": "f64", "d16_mixed": "f32+ff",
-            "batched": "f32", "fwdbwd": "f32"}[w]
+            "d18_fp32": "f32", "batched": "f32", "fwdbwd": "f32"}[w]
 
 
 # ------------------------------------------------------------------- main
@@ -493,7 +516,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--D", type=int, default=None,
+                    help="override D of a single-instance workload (same distribution)")
     args = ap.parse_args()
+    if args.D is not None and args.workload not in SINGLE:
+        ap.error("--D applies to single-instance workloads only")
     if args.steps is None:
         args.steps = DEFAULT_STEPS[args.workload]
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -520,7 +547,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    wl = Workload(args.workload, dev, rank)
+    wl = Workload(args.workload, dev, rank, args.D)
     ms, prof, clk = _time_steps(wl, args.steps, args.warmup, dist)
     value = world * wl.outputs * args.steps / (ms / 1e3)
 
@@ -551,7 +578,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": _dtype_name(args.workload),
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+        "config": {"workload": WORKLOADS[args.workload] if args.D is None else
+                   f"{WORKLOADS[args.workload]} with D overridden to {args.D}",
+                   "name": args.workload, "D": wl.D,
                    "outputs_per_step": wl.outputs, "parallelism": f"replicas{world}",
                    "l2": "working set larger than L2 (129 MB); no flush"
                    if args.workload in ("d20_int64", "d16_fp64", "d16_mixed", "batched", "fwdbwd")
