@@ -119,6 +119,35 @@ hc_status hc_convolve_config(const void* x, const void* y, void* z, int D, hc_dt
                              hc_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * No-allocation form.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory at the call site -- code
+ * running while another framework owns the device's memory pool,
+ * latency-critical loops that cannot afford the device-wide synchronisation
+ * that cudaMalloc and cudaFree imply, or plugin hosts that forbid allocation
+ * once set up.  It computes exactly what hc_convolve computes, under the same
+ * argument rules, but takes no workspace: it works in a fixed array of
+ * HC_NOALLOC_SCRATCH_BYTES in the library's own device memory and calls no
+ * allocating routine.
+ *   - Limit: a problem whose hc_workspace_size exceeds the array is refused
+ *     with HC_ERR_WORKSPACE.  With 16 MiB that allows D <= 15 for HC_INT64
+ *     and HC_FP64, D <= 16 for HC_FP32 and D <= 13 for HC_FP32_MIXED.
+ *   - Every GPU that loads the library holds the array until the process
+ *     exits.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls on one device share the array, which keeps whatever the last
+ *     call left there (nothing in it has to start at zero).  Calls whose work
+ *     overlaps on the GPU -- issued on different streams or from different
+ *     threads without ordering between them -- race on it and produce wrong
+ *     results; order them on one stream or with events.
+ */
+#define HC_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+hc_status hc_convolve_noalloc(const void* x, const void* y, void* z, int D, hc_dtype dtype,
+                              hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Differentiation form.  For z = x * y and an upstream gradient dz = dL/dz
  * (3^D elements):
  *     dx[i] = sum_j dz[i + j] * y[j],     dy[j] = sum_i dz[i + j] * x[i],

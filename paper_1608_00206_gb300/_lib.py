@@ -31,6 +31,7 @@ SIGNATURES = {
     "hc_convolve": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz, _vp]),
     "hc_workspace_size_config": (_sz, [_i, _i, _i, _i]),
     "hc_convolve_config": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp]),
+    "hc_convolve_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "hc_backward_workspace_size": (_sz, [_i, _i]),
     "hc_convolve_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _sz, _vp]),
     "hc_batched_workspace_size": (_sz, [ctypes.POINTER(hc_instance), _i, _i]),
