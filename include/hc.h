@@ -106,17 +106,59 @@ size_t hc_workspace_size(int D, hc_dtype dtype);
 hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dtype,
                       void* workspace, size_t ws_bytes, hc_stream_t stream);
 
-/* Explicit schedule (used by the autotuner and the tests; same result bits as
- * hc_convolve for every valid schedule):
- *   c    : innermost axes fused into one shared-memory tile, 1..9 for HC_FP32,
- *          1..8 otherwise (clamped to D); 0 selects the default.
- *   kmax : most outer axes interpolated per whole-array pass, 1..6; 0 = 6.
- * HC_ERR_ARG for values out of range. */
-size_t hc_workspace_size_config(int D, hc_dtype dtype, int c, int kmax);
+/* ------------------------------------------------------------------------
+ * Schedules.  Every schedule computes the same bits; they differ in how the
+ * D axes are split between shared-memory tiles and passes over HBM.
+ *   HC_SCHED_PASSES  : whole-array passes evaluate the D - c outer axes, one
+ *                      tile kernel handles the c inner axes (evaluation,
+ *                      products, interpolation), whole-array passes
+ *                      interpolate the outer axes, at most k per pass.
+ *   HC_SCHED_CHUNKED : one persistent launch convolves chunks of c + k axes
+ *                      (tiles of c axes, then the k middle axes interpolated
+ *                      while the chunk is in L2); the D - c - k outer axes go
+ *                      through whole-array passes.  D <= c + k: one launch.
+ *   HC_SCHED_DEFAULT : the per-(D, dtype) default (built in: CHUNKED with
+ *                      default sizes; replaced by hc_set_default_schedule,
+ *                      typically with hc_autotune's winner).
+ * Fields: c in 0..9 for HC_FP32, 0..8 otherwise (0 = the largest; clamped to
+ * D); k in 0..6 (0 = 6); cols = columns per whole-array interpolation tile,
+ * 8, 16 or 32 (0 = 32 for 4-byte and 16 for 8-byte intermediates).
+ * HC_ERR_ARG for fields out of range. */
+#define HC_SCHED_DEFAULT 0
+#define HC_SCHED_PASSES 1
+#define HC_SCHED_CHUNKED 2
 
-hc_status hc_convolve_config(const void* x, const void* y, void* z, int D, hc_dtype dtype,
-                             int c, int kmax, void* workspace, size_t ws_bytes,
-                             hc_stream_t stream);
+typedef struct {
+  int kind;
+  int c;
+  int k;
+  int cols;
+} hc_schedule;
+
+size_t hc_workspace_size_schedule(int D, hc_dtype dtype, const hc_schedule* s);
+
+hc_status hc_convolve_schedule(const void* x, const void* y, void* z, int D, hc_dtype dtype,
+                               const hc_schedule* s, void* workspace, size_t ws_bytes,
+                               hc_stream_t stream);
+
+/* The schedule hc_convolve and hc_workspace_size use for (D, dtype);
+ * s = NULL restores the built-in choice.  Process-wide, thread-safe; a
+ * workspace sized before a change may no longer be large enough. */
+hc_status hc_set_default_schedule(int D, hc_dtype dtype, const hc_schedule* s);
+
+hc_status hc_get_default_schedule(int D, hc_dtype dtype, hc_schedule* s);
+
+/* Autotuner: runs every candidate schedule for (D, dtype) on the caller's
+ * buffers (x, y inputs; z output, overwritten; workspace of at least
+ * hc_autotune_workspace_size bytes), `reps` timed runs each after one
+ * warm-up, on `stream` with CUDA events (synchronising), and returns the
+ * fastest in *best and its best time in *best_ms.  It does not install the
+ * winner (see hc_set_default_schedule). */
+size_t hc_autotune_workspace_size(int D, hc_dtype dtype);
+
+hc_status hc_autotune(const void* x, const void* y, void* z, int D, hc_dtype dtype,
+                      void* workspace, size_t ws_bytes, int reps, hc_stream_t stream,
+                      hc_schedule* best, double* best_ms);
 
 /* ------------------------------------------------------------------------
  * No-allocation form.  The paper has no counterpart: this entry point exists
@@ -128,16 +170,18 @@ hc_status hc_convolve_config(const void* x, const void* y, void* z, int D, hc_dt
  * argument rules, but takes no workspace: it works in a fixed array of
  * HC_NOALLOC_SCRATCH_BYTES in the library's own device memory and calls no
  * allocating routine.
- *   - Limit: a problem whose hc_workspace_size exceeds the array is refused
- *     with HC_ERR_WORKSPACE.  With 16 MiB that allows D <= 15 for HC_INT64
- *     and HC_FP64, D <= 16 for HC_FP32 and D <= 13 for HC_FP32_MIXED.
+ *   - It always uses the built-in chunked schedule (whatever default schedule
+ *     is installed).  Limit: a problem whose workspace for that schedule
+ *     exceeds the array is refused with HC_ERR_WORKSPACE.  With 16 MiB that allows D <= 16 for HC_INT64
+ *     and HC_FP64, D <= 17 for HC_FP32 and D <= 13 for HC_FP32_MIXED.
  *   - Every GPU that loads the library holds the array until the process
  *     exits.
  *   - The first call on each device looks up the array's device address
  *     (with that device current); make that first call before any stream
  *     capture.
  *   - All calls on one device share the array, which keeps whatever the last
- *     call left there (nothing in it has to start at zero).  Calls whose work
+ *     call left there; the counters that must start at zero are cleared by
+ *     each call itself, on its stream, before its kernels run.  Calls whose work
  *     overlaps on the GPU -- issued on different streams or from different
  *     threads without ordering between them -- race on it and produce wrong
  *     results; order them on one stream or with events.

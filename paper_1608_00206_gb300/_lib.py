@@ -19,6 +19,16 @@ HC_MAX_D = 24
 _vp, _i, _sz, _cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_char_p
 
 
+HC_SCHED_DEFAULT, HC_SCHED_PASSES, HC_SCHED_CHUNKED = 0, 1, 2
+
+
+class hc_schedule(ctypes.Structure):
+    _fields_ = [("kind", _i), ("c", _i), ("k", _i), ("cols", _i)]
+
+    def as_dict(self):
+        return {"kind": self.kind, "c": self.c, "k": self.k, "cols": self.cols}
+
+
 class hc_instance(ctypes.Structure):
     _fields_ = [("x", _vp), ("y", _vp), ("z", _vp), ("D", _i)]
 
@@ -29,8 +39,13 @@ SIGNATURES = {
     "hc_last_cuda_error": (_cp, []),
     "hc_workspace_size": (_sz, [_i, _i]),
     "hc_convolve": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz, _vp]),
-    "hc_workspace_size_config": (_sz, [_i, _i, _i, _i]),
-    "hc_convolve_config": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp]),
+    "hc_workspace_size_schedule": (_sz, [_i, _i, ctypes.c_void_p]),
+    "hc_convolve_schedule": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_void_p, _vp, _sz, _vp]),
+    "hc_set_default_schedule": (_i, [_i, _i, ctypes.c_void_p]),
+    "hc_get_default_schedule": (_i, [_i, _i, ctypes.c_void_p]),
+    "hc_autotune_workspace_size": (_sz, [_i, _i]),
+    "hc_autotune": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz, _i, _vp, ctypes.c_void_p,
+                         ctypes.POINTER(ctypes.c_double)]),
     "hc_convolve_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "hc_backward_workspace_size": (_sz, [_i, _i]),
     "hc_convolve_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _sz, _vp]),

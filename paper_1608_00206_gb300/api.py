@@ -11,7 +11,7 @@ import ctypes
 
 import torch
 
-from . import _lib
+from . import _lib, tuning
 from ._lib import HCError, check
 
 _DT = {torch.int64: _lib.HC_INT64, torch.float64: _lib.HC_FP64, torch.float32: _lib.HC_FP32}
@@ -48,12 +48,26 @@ def _out_shape(x: torch.Tensor, D: int):
     return (3,) * D if (x.dim() == D and all(s == 2 for s in x.shape) and D > 0) else (3 ** D,)
 
 
-def workspace_size(D: int, dtype: torch.dtype = torch.float32, mixed: bool = False,
-                   c: int = 0, kmax: int = 0) -> int:
-    code = _code(dtype, mixed)
+def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0):
+    """None for the default schedule; else an hc_schedule: m > 0 selects the
+    chunked schedule (c tile axes, m middle axes), otherwise c or kmax select
+    the whole-array-pass schedule; cols alone keeps the default kind."""
+    if m:
+        return _lib.hc_schedule(_lib.HC_SCHED_CHUNKED, c, m, cols)
     if c or kmax:
-        return int(_lib.lib().hc_workspace_size_config(D, code, c, kmax))
-    return int(_lib.lib().hc_workspace_size(D, code))
+        return _lib.hc_schedule(_lib.HC_SCHED_PASSES, c, kmax, cols)
+    if cols:
+        return _lib.hc_schedule(_lib.HC_SCHED_DEFAULT, 0, 0, cols)
+    return None
+
+
+def workspace_size(D: int, dtype: torch.dtype = torch.float32, mixed: bool = False,
+                   c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0) -> int:
+    code = _code(dtype, mixed)
+    s = _schedule(c, kmax, m, cols)
+    if s is None:
+        return int(_lib.lib().hc_workspace_size(D, code))
+    return int(_lib.lib().hc_workspace_size_schedule(D, code, ctypes.byref(s)))
 
 
 def backward_workspace_size(D: int, dtype: torch.dtype = torch.float32) -> int:
@@ -71,29 +85,33 @@ def _workspace(nbytes: int, device, workspace):
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
-def _device_convolve(x, y, z, D, code, workspace, stream, c, kmax):
+def _device_convolve(x, y, z, D, code, workspace, stream, sched):
     lib = _lib.lib()
-    if c or kmax:
-        nbytes = int(lib.hc_workspace_size_config(D, code, c, kmax))
-    else:
+    tuning.ensure_installed(x.device)
+    if sched is None:
         nbytes = int(lib.hc_workspace_size(D, code))
+    else:
+        nbytes = int(lib.hc_workspace_size_schedule(D, code, ctypes.byref(sched)))
     ws = _workspace(nbytes, x.device, workspace)
     st = _stream(x.device, stream)
-    if c or kmax:
-        s = lib.hc_convolve_config(_ptr(x), _ptr(y), _ptr(z), D, code, c, kmax, _ptr(ws),
-                                   nbytes, st)
-    else:
+    if sched is None:
         s = lib.hc_convolve(_ptr(x), _ptr(y), _ptr(z), D, code, _ptr(ws), nbytes, st)
+    else:
+        s = lib.hc_convolve_schedule(_ptr(x), _ptr(y), _ptr(z), D, code, ctypes.byref(sched),
+                                     _ptr(ws), nbytes, st)
     check(s, "hc_convolve")
 
 
 def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, *,
              mixed: bool = False, workspace: torch.Tensor | None = None, stream=None,
-             c: int = 0, kmax: int = 0) -> torch.Tensor:
+             c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0) -> torch.Tensor:
     """z = x * y over {0,1,2}^D.
 
     CUDA tensors: runs on their device and the current (or given) stream,
-    asynchronously.  CPU tensors (the end-to-end path): x and y are copied to
+    asynchronously.  Schedules: default (hc_convolve); m > 0 selects the
+    chunked schedule with m middle axes and c tile axes; otherwise c or kmax
+    select the whole-array-pass schedule; cols sets the interpolation tile
+    width.  CPU tensors (the end-to-end path): x and y are copied to
     the current CUDA device, convolved there, and z is copied back into `out`
     (or a new CPU tensor, pinned if x is pinned); the call returns once z is
     on the host.
@@ -102,6 +120,7 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
         raise ValueError("x and y must have the same dtype and size")
     D = dim_of(x)
     code = _code(x.dtype, mixed)
+    sched = _schedule(c, kmax, m, cols)
     if x.is_cuda:
         if not y.is_cuda or y.device != x.device:
             raise ValueError("x and y must be on the same CUDA device")
@@ -112,14 +131,14 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
         elif not (out.is_cuda and out.is_contiguous() and out.numel() == 3 ** D and
                   out.dtype == x.dtype):
             raise ValueError("out must be a contiguous CUDA tensor of 3^D elements, same dtype")
-        _device_convolve(x, y, out, D, code, workspace, stream, c, kmax)
+        _device_convolve(x, y, out, D, code, workspace, stream, sched)
         return out
     # host buffers: explicit copies around the device call
     dev = torch.device("cuda", torch.cuda.current_device())
     xd = x.contiguous().to(dev, non_blocking=True)
     yd = y.contiguous().to(dev, non_blocking=True)
     zd = torch.empty(3 ** D, dtype=x.dtype, device=dev)
-    _device_convolve(xd, yd, zd, D, code, workspace, stream, c, kmax)
+    _device_convolve(xd, yd, zd, D, code, workspace, stream, sched)
     if out is None:
         out = torch.empty(_out_shape(x, D), dtype=x.dtype, pin_memory=x.is_pinned())
     out.view(-1).copy_(zd, non_blocking=out.is_pinned())

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "hc_common.cuh"
 #include "hc_profile.cuh"
@@ -58,32 +59,7 @@ __global__ void scalar_conv_kernel(const typename M::In* x, const typename M::In
 }
 
 // ---------------------------------------------------------------------------
-// K3 kernel: interpolate k = K1 + K2 consecutive axes of a [hi][3^k][lo]
-// array; a CTA tile is all 3^k rows of L consecutive columns of one h.
-// src and dst may be the same array (every tile reads its elements before
-// writing any; tiles are disjoint).
-template <class M, int K1, int K2, int L, bool FINAL>
-__global__ void __launch_bounds__(256) interp_pass_kernel(const typename M::W* src, void* dst_,
-                                                          long long hi, long long lo) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const long long ctiles = (lo + L - 1) / L;
-  const long long ntiles = hi * ctiles;
-#pragma unroll 1
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long h = tile / ctiles;
-    const long long l0 = (tile - h * ctiles) * L;
-    interp_tile_body<M, K1, K2, L, FINAL, false>(src, dst_, h * p3(K1 + K2) * lo + l0, l0, lo,
-                                                 smem);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Host side.
-
-template <class M>
-struct ColsPerTile {
-  static constexpr int L = (sizeof(typename M::W) == 4) ? 32 : 16;
-};
 
 template <class M>
 static int max_tile_axes() {
@@ -120,36 +96,6 @@ static cudaError_t launch_tile(int C, const typename M::In* X, const typename M:
     case 9:
       if constexpr (sizeof(typename M::W) == 4) return launch_tile_c<M, 9, FINAL>(X, Y, out, ntiles, st);
       return cudaErrorInvalidValue;
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <class M, int K1, int K2, bool FINAL>
-static cudaError_t launch_interp_k(const typename M::W* src, void* dst, long long hi, long long lo,
-                                   cudaStream_t st) {
-  constexpr int L = ColsPerTile<M>::L;
-  const size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
-  auto k = interp_pass_kernel<M, K1, K2, L, FINAL>;
-  ProfileScope prof(st, "interp_pass");
-  cudaError_t e = prep_kernel(k, smem);
-  if (e != cudaSuccess) return e;
-  int threads = K1 > 0 ? 256 : L;
-  if (K1 > 0 && p3(K1) * L < 256 && p3(K2) * L < 256) threads = 128;
-  const long long ntiles = hi * ((lo + L - 1) / L);
-  k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(src, dst, hi, lo);
-  return cudaGetLastError();
-}
-
-template <class M, bool FINAL>
-static cudaError_t launch_interp(int k, const typename M::W* src, void* dst, long long hi,
-                                 long long lo, cudaStream_t st) {
-  switch (k) {
-    case 1: return launch_interp_k<M, 0, 1, FINAL>(src, dst, hi, lo, st);
-    case 2: return launch_interp_k<M, 0, 2, FINAL>(src, dst, hi, lo, st);
-    case 3: return launch_interp_k<M, 0, 3, FINAL>(src, dst, hi, lo, st);
-    case 4: return launch_interp_k<M, 1, 3, FINAL>(src, dst, hi, lo, st);
-    case 5: return launch_interp_k<M, 2, 3, FINAL>(src, dst, hi, lo, st);
-    case 6: return launch_interp_k<M, 3, 3, FINAL>(src, dst, hi, lo, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -261,12 +207,103 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
     const bool last = (i == p.n_interp - 1);
     if (last && mixed_ws)
-      e = launch_interp<M, true>(k, Wbuf, z, hi, lo, st);
+      e = launch_interp<M, true>(k, p.cols, Wbuf, z, hi, lo, st);
     else
-      e = launch_interp<M, false>(k, Wbuf, Wbuf, hi, lo, st);
+      e = launch_interp<M, false>(k, p.cols, Wbuf, Wbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
+  ChunkPlan p;
+  memset(&p, 0, sizeof(p));
+  p.D = D;
+  p.dtype = dt;
+  const int cmax = (dt == HC_FP32) ? 9 : 8;
+  int C = c_req > 0 ? (c_req < cmax ? c_req : cmax) : cmax;
+  if (C > D) C = D;
+  const int mmax = m_req > 0 ? (m_req < 6 ? m_req : 6) : 6;
+  p.C = C;
+  p.m = (D - C) < mmax ? (D - C) : mmax;
+  p.ap = D - C - p.m;
+  const size_t es = elem_size(dt);
+  const size_t wsz = (dt == HC_FP32 || dt == HC_INT64 || dt == HC_FP64) ? es : 8;
+  // The first m - 3 middle axes are evaluated together with the a' outer
+  // axes, leaving at most 3 to evaluate on the fly inside the tiles.
+  p.m_pre = p.m > 3 ? p.m - 3 : 0;
+  const int ev = p.ap + p.m_pre;  // axes evaluated by whole-array passes
+  // whole-array evaluation passes (<= 3 axes each, outer first)
+  for (int d = 0; d < ev; d += 3) {
+    const int k = (ev - d) < 3 ? (ev - d) : 3;
+    p.eval_d0[p.n_eval] = d;
+    p.eval_k[p.n_eval] = k;
+    ++p.n_eval;
+  }
+  size_t xo = ev > 0 ? pow3z(ev) << (D - ev) : 0, tmax = 0;
+  for (int i = 0; i < p.n_eval; ++i) {
+    const int done = p.eval_d0[i] + p.eval_k[i];
+    const bool to_final = ((p.n_eval - 1 - i) % 2) == 0;
+    p.eval_to_final[i] = to_final;
+    const size_t n = pow3z(done) << (D - done);
+    if (!to_final && n > tmax) tmax = n;
+  }
+  // whole-array interpolation passes over the a' outer axes (<= 6, innermost first)
+  if (p.ap > 0) {
+    const int np = (p.ap + 5) / 6;
+    int end = p.ap;
+    for (int i = 0; i < np; ++i) {
+      const int rem = np - i;
+      const int k = (end + rem - 1) / rem;
+      p.interp_d0[i] = end - k;
+      p.interp_k[i] = k;
+      end -= k;
+    }
+    p.n_interp = np;
+  }
+  p.L = wsz == 4 ? 32 : 16;
+  p.units = (long long)pow3z(p.ap);
+  p.n_tiles = (int)pow3z(p.m);
+  if (p.m > 0) {
+    const long long coltiles = ((long long)pow3z(C) + p.L - 1) / p.L;
+    long long cpt = 8192 / ((long long)pow3z(p.m) * p.L);
+    if (cpt < 1) cpt = 1;
+    p.cpt = (int)cpt;
+    p.n_cols = (int)((coltiles + cpt - 1) / cpt);
+  } else {
+    p.cpt = 1;
+    p.n_cols = 0;
+  }
+  p.per_unit = p.n_tiles + p.n_cols;
+  p.total = p.units * p.per_unit;
+  size_t smem = tile_smem_bytes(dt, C);
+  const size_t ismem = p.m >= 4 ? wsz * pow3z(p.m) * p.L : 0;
+  p.smem = smem > ismem ? smem : ismem;
+  size_t off = kWsHeader;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  p.off_ctr = take(8 * (size_t)(p.units + 1));
+  p.off_xo = take(xo * es);
+  p.off_yo = take(xo * es);
+  p.off_tx = take(tmax * es);
+  p.off_ty = take(tmax * es);
+  p.off_w = take((dt == HC_FP32_MIXED && (p.m > 0 || p.ap > 0)) ? pow3z(D) * wsz : 0);
+  p.ws_bytes = off;
+  return p;
+}
+
+cudaError_t chunk_dispatch(const ChunkPlan& p, const void* x, const void* y, void* z,
+                           unsigned char* ws, cudaStream_t st) {
+  switch (p.dtype) {
+    case HC_INT64: return chunk_forward_i64(p, x, y, z, ws, st);
+    case HC_FP64: return chunk_forward_f64(p, x, y, z, ws, st);
+    case HC_FP32: return chunk_forward_f32(p, x, y, z, ws, st);
+    case HC_FP32_MIXED: return chunk_forward_mix(p, x, y, z, ws, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, void* z,
@@ -283,52 +320,189 @@ cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, voi
 }  // namespace hc
 
 // ---------------------------------------------------------------------------
-// C ABI
-
-extern "C" size_t hc_workspace_size(int D, hc_dtype dtype) {
-  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0) return 0;
-  return hc::make_fwd_plan(D, dtype, 0, 0).ws_bytes;
-}
+// Schedules, the default-schedule table and the C ABI
 
 namespace hc {
 
+static std::mutex g_sched_mu;
+static hc_schedule g_default[HC_MAX_D + 1][4];
+static bool g_has_default[HC_MAX_D + 1][4];
+
+bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
+  const int cmax = dtype == HC_FP32 ? 9 : 8;
+  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_CHUNKED) return false;
+  if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
+  return s.cols == 0 || s.cols == 8 || s.cols == 16 || s.cols == 32;
+}
+
+hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
+  if (s && s->kind != HC_SCHED_DEFAULT) return *s;
+  hc_schedule r = {HC_SCHED_CHUNKED, 0, 0, 0};
+  if (D >= 0 && D <= HC_MAX_D && dtype >= 0 && dtype < 4) {
+    std::lock_guard<std::mutex> g(g_sched_mu);
+    if (g_has_default[D][dtype]) r = g_default[D][dtype];
+  }
+  if (s) {  // a DEFAULT schedule may still fix the column width
+    if (s->cols) r.cols = s->cols;
+  }
+  return r;
+}
+
+static FwdPlan passes_plan(int D, hc_dtype dt, const hc_schedule& s) {
+  FwdPlan p = make_fwd_plan(D, dt, s.c, s.k);
+  p.cols = s.cols;
+  return p;
+}
+
+static ChunkPlan chunked_plan(int D, hc_dtype dt, const hc_schedule& s) {
+  ChunkPlan p = make_chunk_plan(D, dt, s.c, s.k);
+  p.cols = s.cols;
+  return p;
+}
+
+size_t schedule_ws(int D, hc_dtype dtype, const hc_schedule& s) {
+  if (D < 0 || D > HC_MAX_D || elem_size(dtype) == 0) return 0;
+  if (s.kind == HC_SCHED_PASSES || D == 0) return passes_plan(D, dtype, s).ws_bytes;
+  return chunked_plan(D, dtype, s).ws_bytes;
+}
+
 hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtype dtype,
-                           void* workspace, size_t ws_bytes, cudaStream_t stream, int c_req,
-                           int kmax_req) {
+                           void* workspace, size_t ws_bytes, cudaStream_t stream,
+                           const hc_schedule* sched) {
   if (D < 0 || D > HC_MAX_D) return HC_ERR_ARG;
   const size_t es = elem_size(dtype);
   if (es == 0) return HC_ERR_DTYPE;
+  if (sched && !schedule_valid(*sched, dtype)) return HC_ERR_ARG;
   if (!x || !y || !z) return HC_ERR_ARG;
   if (!aligned(x, 16) || !aligned(y, 16) || !aligned(z, 16)) return HC_ERR_ALIGN;
-  const FwdPlan p = make_fwd_plan(D, dtype, c_req, kmax_req);
-  if (ws_bytes < p.ws_bytes) return HC_ERR_WORKSPACE;
-  if (p.ws_bytes > 0 && !workspace) return HC_ERR_ARG;
+  const hc_schedule s = resolve_schedule(D, dtype, sched);
+  const size_t need = schedule_ws(D, dtype, s);
+  if (ws_bytes < need) return HC_ERR_WORKSPACE;
+  if (need > 0 && !workspace) return HC_ERR_ARG;
   if (workspace && !aligned(workspace, 256)) return HC_ERR_ALIGN;
   const size_t nx = es << D, nz = es * pow3z(D);
   if (overlaps(z, nz, x, nx) || overlaps(z, nz, y, nx)) return HC_ERR_ALIAS;
-  if (workspace && p.ws_bytes > 0 &&
-      (overlaps(workspace, p.ws_bytes, z, nz) || overlaps(workspace, p.ws_bytes, x, nx) ||
-       overlaps(workspace, p.ws_bytes, y, nx)))
+  if (workspace && need > 0 &&
+      (overlaps(workspace, need, z, nz) || overlaps(workspace, need, x, nx) ||
+       overlaps(workspace, need, y, nx)))
     return HC_ERR_ALIAS;
-  return record_cuda_error(forward_dispatch(p, x, y, z, (unsigned char*)workspace, stream));
+  if (s.kind == HC_SCHED_PASSES || D == 0)
+    return record_cuda_error(
+        forward_dispatch(passes_plan(D, dtype, s), x, y, z, (unsigned char*)workspace, stream));
+  return record_cuda_error(
+      chunk_dispatch(chunked_plan(D, dtype, s), x, y, z, (unsigned char*)workspace, stream));
+}
+
+// Candidate schedules of the autotuner for (D, dtype).
+static std::vector<hc_schedule> tune_candidates(int D, hc_dtype dtype) {
+  std::vector<hc_schedule> v;
+  const int cmax = dtype == HC_FP32 ? 9 : 8;
+  if (D <= cmax) {
+    v.push_back({HC_SCHED_CHUNKED, 0, 0, 0});
+    return v;
+  }
+  const int cols[3] = {8, 16, 32};
+  for (int c = cmax - 1; c <= cmax; ++c) {
+    for (int k = 3; k <= 6; ++k)
+      for (int ci = 0; ci < 3; ++ci) {
+        v.push_back({HC_SCHED_PASSES, c, k, cols[ci]});
+        v.push_back({HC_SCHED_CHUNKED, c, k, cols[ci]});
+      }
+  }
+  return v;
 }
 
 }  // namespace hc
 
-extern "C" size_t hc_workspace_size_config(int D, hc_dtype dtype, int c, int kmax) {
-  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0) return 0;
-  return hc::make_fwd_plan(D, dtype, c, kmax).ws_bytes;
+extern "C" size_t hc_workspace_size(int D, hc_dtype dtype) {
+  return hc::schedule_ws(D, dtype, hc::resolve_schedule(D, dtype, nullptr));
 }
 
-extern "C" hc_status hc_convolve_config(const void* x, const void* y, void* z, int D,
-                                        hc_dtype dtype, int c, int kmax, void* workspace,
-                                        size_t ws_bytes, hc_stream_t stream) {
-  if (c < 0 || c > (dtype == HC_FP32 ? 9 : 8) || kmax < 0 || kmax > 6) return HC_ERR_ARG;
-  return hc::convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, (cudaStream_t)stream, c,
-                              kmax);
+extern "C" size_t hc_workspace_size_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
+  if (s && !hc::schedule_valid(*s, dtype)) return 0;
+  return hc::schedule_ws(D, dtype, hc::resolve_schedule(D, dtype, s));
 }
 
 extern "C" hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dtype,
                                  void* workspace, size_t ws_bytes, hc_stream_t stream) {
-  return hc::convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, (cudaStream_t)stream, 0, 0);
+  return hc::convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, (cudaStream_t)stream,
+                              nullptr);
+}
+
+extern "C" hc_status hc_convolve_schedule(const void* x, const void* y, void* z, int D,
+                                          hc_dtype dtype, const hc_schedule* s, void* workspace,
+                                          size_t ws_bytes, hc_stream_t stream) {
+  if (!s) return HC_ERR_ARG;
+  return hc::convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, (cudaStream_t)stream, s);
+}
+
+extern "C" hc_status hc_set_default_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
+  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0) return HC_ERR_ARG;
+  if (s && (!hc::schedule_valid(*s, dtype) || s->kind == HC_SCHED_DEFAULT)) return HC_ERR_ARG;
+  std::lock_guard<std::mutex> g(hc::g_sched_mu);
+  hc::g_has_default[D][dtype] = s != nullptr;
+  if (s) hc::g_default[D][dtype] = *s;
+  return HC_OK;
+}
+
+extern "C" hc_status hc_get_default_schedule(int D, hc_dtype dtype, hc_schedule* s) {
+  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0 || !s) return HC_ERR_ARG;
+  *s = hc::resolve_schedule(D, dtype, nullptr);
+  return HC_OK;
+}
+
+extern "C" size_t hc_autotune_workspace_size(int D, hc_dtype dtype) {
+  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0) return 0;
+  size_t m = hc::schedule_ws(D, dtype, hc::resolve_schedule(D, dtype, nullptr));
+  for (const hc_schedule& s : hc::tune_candidates(D, dtype)) {
+    const size_t w = hc::schedule_ws(D, dtype, s);
+    if (w > m) m = w;
+  }
+  return m;
+}
+
+extern "C" hc_status hc_autotune(const void* x, const void* y, void* z, int D, hc_dtype dtype,
+                                 void* workspace, size_t ws_bytes, int reps, hc_stream_t stream,
+                                 hc_schedule* best, double* best_ms) {
+  using namespace hc;
+  if (D < 0 || D > HC_MAX_D || elem_size(dtype) == 0 || reps < 1) return HC_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) return record_cuda_error(ce);
+  hc_schedule win = {HC_SCHED_CHUNKED, 0, 0, 0};
+  double win_ms = -1.0;
+  hc_status status = HC_OK;
+  for (const hc_schedule& s : tune_candidates(D, dtype)) {
+    if (schedule_ws(D, dtype, s) > ws_bytes) continue;
+    status = convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, st, &s);  // warm-up
+    if (status != HC_OK) break;
+    double t_min = -1.0;
+    for (int r = 0; r < reps && status == HC_OK; ++r) {
+      cudaEventRecord(e0, st);
+      status = convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, st, &s);
+      cudaEventRecord(e1, st);
+      ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        status = record_cuda_error(ce);
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (t_min < 0.0 || ms < t_min) t_min = ms;
+    }
+    if (status != HC_OK) break;
+    if (win_ms < 0.0 || t_min < win_ms) {
+      win_ms = t_min;
+      win = s;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != HC_OK) return status;
+  if (win_ms < 0.0) return HC_ERR_WORKSPACE;  // no candidate fitted the workspace
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return HC_OK;
 }

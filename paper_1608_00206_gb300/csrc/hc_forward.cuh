@@ -17,7 +17,43 @@ struct FwdPlan {
   int interp_d0[HC_MAX_D], interp_k[HC_MAX_D];
   size_t off_xo, off_yo, off_tx, off_ty, off_w;
   size_t ws_bytes;
+  int cols;  // columns per whole-array interpolation tile (0 = default)
 };
+
+// The default schedule ("chunked"): the a' = D - C - m outermost axes are
+// evaluated by whole-array passes, then one persistent launch convolves the
+// 3^a' chunks of C + m axes (tiles of C axes, m <= 6 middle axes
+// interpolated while the chunk is in L2), then whole-array passes
+// interpolate the a' outer axes.  For D <= C + 6 it is a single launch.
+struct ChunkPlan {
+  int D;
+  hc_dtype dtype;
+  int C, m, ap;
+  int m_pre;  // middle axes evaluated by the whole-array passes (with the a' outer axes)
+  int n_eval;
+  int eval_d0[HC_MAX_D], eval_k[HC_MAX_D];
+  bool eval_to_final[HC_MAX_D];
+  int n_interp;
+  int interp_d0[HC_MAX_D], interp_k[HC_MAX_D];
+  long long units, per_unit, total;
+  int n_tiles, n_cols, cpt, L;
+  size_t smem;
+  size_t off_ctr, off_xo, off_yo, off_tx, off_ty, off_w;
+  size_t ws_bytes;
+  int cols;  // columns per whole-array interpolation tile (0 = default)
+};
+
+// c_req: tile axes (0 = default); m_req: middle axes per chunk (0 = default).
+ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req);
+
+cudaError_t chunk_forward_i64(const ChunkPlan& p, const void* x, const void* y, void* z,
+                              unsigned char* ws, cudaStream_t st);
+cudaError_t chunk_forward_f64(const ChunkPlan& p, const void* x, const void* y, void* z,
+                              unsigned char* ws, cudaStream_t st);
+cudaError_t chunk_forward_f32(const ChunkPlan& p, const void* x, const void* y, void* z,
+                              unsigned char* ws, cudaStream_t st);
+cudaError_t chunk_forward_mix(const ChunkPlan& p, const void* x, const void* y, void* z,
+                              unsigned char* ws, cudaStream_t st);
 
 // c_req, kmax_req <= 0 select the defaults (largest tile, 6 axes per pass).
 FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);
@@ -25,8 +61,13 @@ FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);
 cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, void* z,
                              unsigned char* ws, cudaStream_t st);
 
+// Validated schedule with kind resolved (1 = passes, 2 = chunked).
+bool schedule_valid(const hc_schedule& s, hc_dtype dtype);
+hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s);
+size_t schedule_ws(int D, hc_dtype dtype, const hc_schedule& s);
+
 hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtype dtype,
-                           void* workspace, size_t ws_bytes, cudaStream_t stream, int c_req,
-                           int kmax_req);
+                           void* workspace, size_t ws_bytes, cudaStream_t stream,
+                           const hc_schedule* sched);
 
 }  // namespace hc

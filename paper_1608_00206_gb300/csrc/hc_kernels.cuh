@@ -3,6 +3,7 @@
 #pragma once
 
 #include "hc_common.cuh"
+#include "hc_tile.cuh"
 #include "hc_profile.cuh"
 
 namespace hc {
@@ -77,6 +78,78 @@ inline cudaError_t launch_eval(int K, const typename M::In* sx, const typename M
     case 1: return launch_eval_k<M, 1>(sx, sy, dx, dy, hi, lo, st);
     case 2: return launch_eval_k<M, 2>(sx, sy, dx, dy, hi, lo, st);
     case 3: return launch_eval_k<M, 3>(sx, sy, dx, dy, hi, lo, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// K3 kernel: interpolate k = K1 + K2 consecutive axes of a [hi][3^k][lo]
+// array; a CTA tile is all 3^k rows of L consecutive columns of one h.
+// src and dst may be the same array (every tile reads its elements before
+// writing any; tiles are disjoint).
+template <class M, int K1, int K2, int L, bool FINAL>
+__global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256) interp_pass_kernel(const typename M::W* src, void* dst_,
+                                                          long long hi, long long lo) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const long long ctiles = (lo + L - 1) / L;
+  const long long ntiles = hi * ctiles;
+#pragma unroll 1
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long h = tile / ctiles;
+    const long long l0 = (tile - h * ctiles) * L;
+    interp_tile_body<M, K1, K2, L, FINAL, false>(src, dst_, h * p3(K1 + K2) * lo + l0, l0, lo,
+                                                 smem);
+  }
+}
+
+// Columns per whole-array interpolation tile (the schedule's `cols`).
+template <class M>
+inline int default_cols() {
+  return sizeof(typename M::W) == 4 ? 32 : 16;
+}
+
+// k = K1 + K2 axes per pass; K1 > 0: a CTA of 27 * L threads (one pencil per
+// thread and round) owns an L-column tile; K1 == 0: 256 columns per CTA, one
+// column per thread.
+template <class M, int K1, int K2, int L, bool FINAL>
+inline cudaError_t launch_interp_kl(const typename M::W* src, void* dst, long long hi,
+                                    long long lo, cudaStream_t st) {
+  constexpr int LT = K1 > 0 ? L : 256;
+  const size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
+  auto k = interp_pass_kernel<M, K1, K2, LT, FINAL>;
+  ProfileScope prof(st, "interp_pass");
+  cudaError_t e = prep_kernel(k, smem);
+  if (e != cudaSuccess) return e;
+  int threads = K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256;
+  if (threads > 1024) threads = 1024;
+  const long long ntiles = hi * ((lo + LT - 1) / LT);
+  k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(src, dst, hi, lo);
+  return cudaGetLastError();
+}
+
+template <class M, int K1, int K2, bool FINAL>
+inline cudaError_t launch_interp_k(int cols, const typename M::W* src, void* dst, long long hi,
+                                   long long lo, cudaStream_t st) {
+  if constexpr (K1 == 0) return launch_interp_kl<M, 0, K2, 256, FINAL>(src, dst, hi, lo, st);
+  switch (cols) {
+    case 8: return launch_interp_kl<M, K1, K2, 8, FINAL>(src, dst, hi, lo, st);
+    case 16: return launch_interp_kl<M, K1, K2, 16, FINAL>(src, dst, hi, lo, st);
+    case 32: return launch_interp_kl<M, K1, K2, 32, FINAL>(src, dst, hi, lo, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class M, bool FINAL>
+inline cudaError_t launch_interp(int k, int cols, const typename M::W* src, void* dst,
+                                 long long hi, long long lo, cudaStream_t st) {
+  if (cols <= 0) cols = default_cols<M>();
+  switch (k) {
+    case 1: return launch_interp_k<M, 0, 1, FINAL>(cols, src, dst, hi, lo, st);
+    case 2: return launch_interp_k<M, 0, 2, FINAL>(cols, src, dst, hi, lo, st);
+    case 3: return launch_interp_k<M, 0, 3, FINAL>(cols, src, dst, hi, lo, st);
+    case 4: return launch_interp_k<M, 1, 3, FINAL>(cols, src, dst, hi, lo, st);
+    case 5: return launch_interp_k<M, 2, 3, FINAL>(cols, src, dst, hi, lo, st);
+    case 6: return launch_interp_k<M, 3, 3, FINAL>(cols, src, dst, hi, lo, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -45,14 +45,17 @@ extern "C" hc_status hc_convolve_noalloc(const void* x, const void* y, void* z, 
                                          hc_dtype dtype, hc_stream_t stream) {
   if (D < 0 || D > HC_MAX_D) return HC_ERR_ARG;
   if (hc::elem_size(dtype) == 0) return HC_ERR_DTYPE;
-  // Problems whose workspace does not fit the fixed array are refused.
-  if (hc_workspace_size(D, dtype) > kScratchBytes) return HC_ERR_WORKSPACE;
+  // The built-in chunked schedule, whatever default is installed, so that the
+  // size limit stays the documented one.  Problems whose workspace does not
+  // fit the fixed array are refused.
+  const hc_schedule builtin = {HC_SCHED_CHUNKED, 0, 0, 0};
+  if (hc_workspace_size_schedule(D, dtype, &builtin) > kScratchBytes) return HC_ERR_WORKSPACE;
   void* scratch = nullptr;
   const hc_status s = scratch_for_current_device(&scratch);
   if (s != HC_OK) return s;
   // Same validation and kernels as hc_convolve, with the array as workspace.
-  // Nothing in a forward workspace has to start at zero, so the contents left
-  // by the previous call are simply overwritten.
+  // The schedule clears the counters it needs at zero itself (a memset on the
+  // stream); everything else left by the previous call is overwritten.
   return hc::convolve_checked(x, y, z, D, dtype, scratch, kScratchBytes, (cudaStream_t)stream,
-                              0, 0);
+                              &builtin);
 }

@@ -1,0 +1,383 @@
+// Persistent ticket engine shared by the batched kernel (many independent
+// convolutions) and the chunked forward kernel (one large convolution cut
+// into chunks of C + m axes).
+//
+// A unit is one convolution of C + m axes.  Its inputs arrive with the first
+// m_pre of the m outer ("middle") axes already evaluated: rows
+// [3^m_pre][2^(m - m_pre)][2^C]; the remaining m - m_pre <= 6 middle axes are
+// evaluated on the fly inside the tile loads.  A unit contributes 3^m tile tickets (tile_body: inner
+// evaluation, products, inner interpolation of C axes, written to the unit's
+// W region) followed by column tickets (the m middle axes interpolated over
+// cpt column tiles of L columns each).
+//
+// Tickets are claimed in increasing order from one global counter.  A column
+// ticket waits only for tile tickets of its own unit, which have smaller
+// numbers; a CTA claims its next ticket early only
+// while it cannot be waiting (during a tile, or after its wait ended), so a
+// claimed ticket always belongs to a CTA that will reach it, the smallest
+// unfinished claimed ticket only ever waits on finished work, and every wait
+// ends.  The waits are
+// bounded anyway: after ~1 s a wait gives up, marks its unit's counter and
+// records HC_ERR_TIMEOUT in the workspace status word; later waiters on the
+// same unit give up at once.
+//
+// A unit's column tickets follow its tiles within about one unit's worth of
+// tickets, so its 3^(C+m) intermediate is still in L2 when they read it back
+// (through L2 only: ld.global.cg).
+#pragma once
+
+#include <type_traits>
+
+#include "hc_common.cuh"
+#include "hc_tile.cuh"
+
+namespace hc {
+
+struct UnitDesc {
+  const void* x;    // 2^(C+m) elements
+  const void* y;
+  void* w;          // tile outputs, 3^(C+m) W elements
+  void* z;          // column outputs (Out elements when the columns finish the
+                    // result in another type, else the same array as w)
+  long long first;  // first ticket of the unit
+  int C, m;
+  int n_tiles;      // 3^m
+  int n_cols;       // column tickets
+  int cpt;          // column tiles per column ticket
+  int need;         // finished tiles a column ticket waits for (n_tiles)
+  int m_pre;        // leading middle axes already evaluated in x, y
+  int pad;
+};
+
+// Units generated arithmetically: unit u reads x + u * in_stride and writes
+// w + u * out_stride (and z + u * out_stride).
+struct UniformUnits {
+  const void* x;
+  const void* y;
+  void* w;
+  void* z;
+  long long in_stride, out_stride, per_unit;
+  int C, m, n_tiles, n_cols, cpt, need, m_pre, units;
+};
+
+constexpr unsigned long long kSpinLimit = 1ull << 22;  // x >= 256 ns sleeps: ~1 s
+constexpr unsigned long long kPoison = 1ull << 63;
+
+// Element i of operand op's row, evaluated on the digit-1 axes at the
+// tile's middle digits: digit 0 / 2 selects bit 0 / 1 (folded into `base`);
+// the m axes with digit 1 are summed as a pairwise tree whose first level
+// pairs the outermost of them (the recursion evaluates axis 1 before axis 2,
+// so its sums nest that way).  Leaves are loaded in blocks of 2^min(m,3)
+// independent loads (one memory round trip per block); a block is a subtree
+// of the three outermost digit-1 axes, and blocks are combined in order.
+template <class M>
+struct OtfLoader {
+  typedef typename M::In In;
+  const In* x;
+  const In* y;
+  long long base;       // fixed bits, as a flat offset
+  long long stride[6];  // flat offsets of the digit-1 axes, outermost first
+  int m;
+  __device__ __forceinline__ In operator()(int op, int i) const {
+    const In* s = (op ? y : x) + base + i;
+    if (m == 0) return s[0];
+    const int mb = m < 3 ? m : 3;
+    long long lo_off[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      long long o = 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < mb && ((j >> q) & 1)) o += stride[q];
+      lo_off[j] = o;
+    }
+    const int nblocks = 1 << (m - mb);
+    In stack[4];
+    int sp = 0;
+#pragma unroll 1
+    for (int blk = 0; blk < nblocks; ++blk) {
+      long long hi = 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q + 3 < m && ((blk >> q) & 1)) hi += stride[q + 3];
+      In v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < (1 << mb)) v[j] = s[hi + lo_off[j]];
+      In r;
+      if (mb == 1) {
+        r = M::add(v[0], v[1]);
+      } else if (mb == 2) {
+        r = M::add(M::add(v[0], v[1]), M::add(v[2], v[3]));
+      } else {
+        r = M::add(M::add(M::add(v[0], v[1]), M::add(v[2], v[3])),
+                   M::add(M::add(v[4], v[5]), M::add(v[6], v[7])));
+      }
+#pragma unroll 1
+      for (int t = blk; t & 1; t >>= 1) r = M::add(stack[--sp], r);
+      stack[sp++] = r;
+    }
+    return stack[0];
+  }
+};
+
+template <class M>
+struct PersistCols {
+  static constexpr int L = sizeof(typename M::W) == 4 ? 32 : 16;
+};
+
+template <class M>
+__host__ __device__ constexpr int persist_cols() {
+  return PersistCols<M>::L;
+}
+
+// Tile of runtime size C (batched units of any D).
+template <class M, bool FINAL>
+__device__ __forceinline__ void tile_any_c(int C, const OtfLoader<M>& ld, void* out,
+                                           unsigned char* smem) {
+  switch (C) {
+    case 0:  // D = 0: z[0] = x[0] * y[0]
+      if constexpr (FINAL) {
+        if (threadIdx.x == 0) *(typename M::Out*)out = M::out(M::mul(ld(0, 0), ld(1, 0)));
+      }
+      break;
+    case 1: tile_body<M, 1, FINAL>(ld, out, smem); break;
+    case 2: tile_body<M, 2, FINAL>(ld, out, smem); break;
+    case 3: tile_body<M, 3, FINAL>(ld, out, smem); break;
+    case 4: tile_body<M, 4, FINAL>(ld, out, smem); break;
+    case 5: tile_body<M, 5, FINAL>(ld, out, smem); break;
+    case 6: tile_body<M, 6, FINAL>(ld, out, smem); break;
+    case 7: tile_body<M, 7, FINAL>(ld, out, smem); break;
+    case 8: tile_body<M, 8, FINAL>(ld, out, smem); break;
+    case 9:
+      if constexpr (sizeof(typename M::W) == 4) tile_body<M, 9, FINAL>(ld, out, smem);
+      break;
+  }
+}
+
+// Interpolation of the m middle axes over one column tile [l0, l0 + L) of a
+// [3^m][lo] array (src and dst offset to the unit).
+template <class M, bool FIN>
+__device__ __forceinline__ void cols_interp(int m, const typename M::W* src, void* dst,
+                                            long long l0, long long lo, unsigned char* smem) {
+  constexpr int L = PersistCols<M>::L;
+  switch (m) {
+    case 1: interp_tile_body<M, 0, 1, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
+    case 2: interp_tile_body<M, 0, 2, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
+    case 3: interp_tile_body<M, 0, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
+    case 4: interp_tile_body<M, 1, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
+    case 5: interp_tile_body<M, 2, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
+    case 6: interp_tile_body<M, 3, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
+  }
+}
+
+// m <= 3 middle axes: every thread takes whole columns of [c0, c1), no
+// shared memory.
+template <class M, int K, bool FIN>
+__device__ __forceinline__ void cols_small_k(const typename M::W* src, void* dst, long long c0,
+                                             long long c1, long long lo) {
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+#pragma unroll 1
+  for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    W v[p3(K)];
+#pragma unroll
+    for (int j = 0; j < p3(K); ++j) v[j] = ldw<true>(src + j * lo + c);
+    interp_pencil<M, K>(v);
+    if constexpr (FIN) {
+#pragma unroll
+      for (int j = 0; j < p3(K); ++j) reinterpret_cast<Out*>(dst)[j * lo + c] = M::out(v[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < p3(K); ++j) reinterpret_cast<W*>(dst)[j * lo + c] = v[j];
+    }
+  }
+}
+
+template <class M, bool FIN>
+__device__ __forceinline__ void cols_small(int m, const typename M::W* src, void* dst,
+                                           long long c0, long long c1, long long lo) {
+  switch (m) {
+    case 1: cols_small_k<M, 1, FIN>(src, dst, c0, c1, lo); break;
+    case 2: cols_small_k<M, 2, FIN>(src, dst, c0, c1, lo); break;
+    case 3: cols_small_k<M, 3, FIN>(src, dst, c0, c1, lo); break;
+  }
+}
+
+// Ticket order.  Unit u's tiles come before its column tickets, and the
+// column tickets of unit u come after the tiles of unit u + 1:
+//   tiles(0), tiles(1), cols(0), tiles(2), cols(1), ..., cols(units - 1).
+// By the time a column ticket is claimed its unit's tiles were claimed one
+// unit earlier, so it rarely waits; two units are in L2 at a time.
+__device__ __forceinline__ void uniform_ticket(long long t, const UniformUnits& uu, int& u,
+                                               long long& local) {
+  const long long nt = uu.n_tiles, per = uu.per_unit;
+  if (t < nt) {
+    u = 0;
+    local = t;
+    return;
+  }
+  const long long tp = t - nt;
+  if (tp < (long long)(uu.units - 1) * per) {
+    const long long b = tp / per, r = tp - b * per;
+    u = (int)(r < nt ? b + 1 : b);
+    local = r;  // a column's local index is n_tiles + its column number = r
+  } else {
+    u = uu.units - 1;
+    local = nt + (tp - (long long)(uu.units - 1) * per);
+  }
+}
+
+// counters[0]: ticket counter; counters[1 + u]: finished tiles of unit u.
+// CT > 0: every unit has C = CT (compile-time tile); CT < 0: per-unit C.
+// UNIFORM: units from `uu`; else (unit, local) = ticket_map[t], unit desc[unit].
+// FIN: column tickets write Out elements to z (float-float -> binary32).
+template <class M, int CT, bool UNIFORM, bool FIN>
+__device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ desc,
+                                                const int2* __restrict__ ticket_map,
+                                                const UniformUnits& uu, long long total,
+                                                unsigned long long* counters, WsHeader* hdr,
+                                                unsigned char* smem) {
+  typedef typename M::In In;
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  typedef typename std::conditional<FIN, Out, W>::type ZT;
+  // Broadcast slots, double-buffered by iteration parity: thread 0 rewrites a
+  // slot two iterations later, after every thread has passed the barrier at
+  // the top of the iteration in between.
+  __shared__ long long s_ticket[2], s_local[2];
+  __shared__ int s_unit[2], s_ok[2];
+  const int tid = threadIdx.x;
+  // Thread 0 claims the next ticket early (its result is first read at the
+  // top of the next iteration), but never while its CTA may still wait: a
+  // CTA stalled in a wait must not hold a claimed ticket that others wait on.
+  long long next = -1;
+#pragma unroll 1
+  for (int it = 0;; it ^= 1) {
+    if (tid == 0) {
+      const long long t = next >= 0 ? next : (long long)atomicAdd(&counters[0], 1ull);
+      next = -1;
+      int u = 0;
+      long long local = 0;
+      if (t < total) {
+        if constexpr (UNIFORM) {
+          uniform_ticket(t, uu, u, local);
+        } else {
+          const int2 e = ticket_map[t];
+          u = e.x;
+          local = e.y;
+        }
+      }
+      s_ticket[it] = t;
+      s_unit[it] = u;
+      s_local[it] = local;
+    }
+    __syncthreads();
+    const long long t = s_ticket[it];
+    if (t >= total) break;
+    const int u = s_unit[it];
+    const long long local = s_local[it];
+    UnitDesc d;
+    if constexpr (UNIFORM) {
+      d.x = (const In*)uu.x + u * uu.in_stride;
+      d.y = (const In*)uu.y + u * uu.in_stride;
+      d.w = (W*)uu.w + u * uu.out_stride;
+      d.z = (ZT*)uu.z + u * uu.out_stride;
+      d.C = uu.C;
+      d.m = uu.m;
+      d.n_tiles = uu.n_tiles;
+      d.n_cols = uu.n_cols;
+      d.cpt = uu.cpt;
+      d.need = uu.need;
+      d.m_pre = uu.m_pre;
+    } else {
+      d = desc[u];
+    }
+    const int C = CT > 0 ? CT : d.C;
+    if (local < d.n_tiles) {
+      if (tid == 0) next = (long long)atomicAdd(&counters[0], 1ull);  // tiles never wait
+      // ---- tile at middle digits alpha = local (the unit's axis 1 most
+      // significant): m_pre pre-evaluated digits (a row index), then the
+      // m - m_pre on-the-fly ones
+      const int m_otf = d.m - d.m_pre;
+      const long long p3otf = pow3_dev(m_otf);
+      OtfLoader<M> ld;
+      ld.x = (const In*)d.x;
+      ld.y = (const In*)d.y;
+      ld.base = (local / p3otf) << (C + m_otf);
+      ld.m = 0;
+      long long w3 = p3otf / 3;
+      const long long otf = local % p3otf;
+      for (int q = 0; q < m_otf; ++q) {
+        const int digit = (int)((otf / w3) % 3);
+        w3 /= 3;
+        const long long bit = (long long)1 << (C + (m_otf - 1 - q));
+        if (digit == 2) ld.base += bit;
+        if (digit == 1) ld.stride[ld.m++] = bit;
+      }
+      if (d.m == 0) {
+        if constexpr (CT > 0)
+          tile_body<M, (CT > 0 ? CT : 1), true>(ld, (Out*)d.z, smem);
+        else
+          tile_any_c<M, true>(C, ld, (Out*)d.z, smem);
+      } else {
+        W* out = (W*)d.w + local * pow3_dev(C);
+        if constexpr (CT > 0)
+          tile_body<M, (CT > 0 ? CT : 1), false>(ld, out, smem);
+        else
+          tile_any_c<M, false>(C, ld, out, smem);
+        // release: the barrier orders every thread's stores before thread 0's
+        // fence, which orders them before the counter increment
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          atomicAdd(&counters[1 + u], 1ull);
+        }
+      }
+    } else {
+      // ---- column ticket: interpolate the m middle axes
+      if (tid == 0) {
+        volatile unsigned long long* done = &counters[1 + u];
+        unsigned long long spins = 0;
+        int ok = 1;
+        for (;;) {
+          const unsigned long long v = *done;
+          if (v & kPoison) {
+            ok = 0;
+            break;
+          }
+          if (v >= (unsigned long long)d.need) break;
+          __nanosleep(256);
+          if (++spins > kSpinLimit) {
+            ok = 0;
+            atomicOr(&counters[1 + u], kPoison);
+            atomicExch(&hdr->status, (unsigned int)HC_ERR_TIMEOUT);
+            atomicExch(&hdr->where, (unsigned int)u);
+            break;
+          }
+        }
+        __threadfence();
+        s_ok[it] = ok;
+        next = (long long)atomicAdd(&counters[0], 1ull);  // the wait is over
+      }
+      __syncthreads();
+      if (s_ok[it]) {
+        constexpr int L = PersistCols<M>::L;
+        const long long lo = pow3_dev(C);
+        const long long c0 = (local - d.n_tiles) * d.cpt * L;
+        const long long c1 = (c0 + (long long)d.cpt * L < lo) ? c0 + (long long)d.cpt * L : lo;
+        if (d.m <= 3) {
+          cols_small<M, FIN>(d.m, (const W*)d.w, d.z, c0, c1, lo);
+        } else {
+#pragma unroll 1
+          for (long long l0 = c0; l0 < c1; l0 += L)
+            cols_interp<M, FIN>(d.m, (const W*)d.w, d.z, l0, lo, smem);
+        }
+      }
+    }
+    // No barrier here: every smem-using body above ends with one, and the
+    // broadcast slots are double-buffered.
+  }
+}
+
+}  // namespace hc

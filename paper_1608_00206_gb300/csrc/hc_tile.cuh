@@ -63,6 +63,33 @@ struct TileSmem {
 // Loader: ld(op, i) returns element i of the tile's operand row (op 0 = x,
 // 1 = y), already evaluated on the outer axes.  out_tile: the tile's 3^C
 // outputs.  smem: TileSmem<M, C>::bytes of shared memory.
+template <class M>
+inline size_t tile_smem_bytes_m(int C) {
+  switch (C) {
+    case 1: return TileSmem<M, 1>::bytes;
+    case 2: return TileSmem<M, 2>::bytes;
+    case 3: return TileSmem<M, 3>::bytes;
+    case 4: return TileSmem<M, 4>::bytes;
+    case 5: return TileSmem<M, 5>::bytes;
+    case 6: return TileSmem<M, 6>::bytes;
+    case 7: return TileSmem<M, 7>::bytes;
+    case 8: return TileSmem<M, 8>::bytes;
+    case 9: return TileSmem<M, 9>::bytes;
+  }
+  return 0;
+}
+
+// Shared memory of tile_body for a dtype and tile size C.
+inline size_t tile_smem_bytes(hc_dtype dt, int C) {
+  switch (dt) {
+    case HC_INT64: return tile_smem_bytes_m<ModeI64>(C);
+    case HC_FP64: return tile_smem_bytes_m<ModeF64>(C);
+    case HC_FP32: return tile_smem_bytes_m<ModeF32>(C);
+    case HC_FP32_MIXED: return tile_smem_bytes_m<ModeMixed>(C);
+  }
+  return 0;
+}
+
 template <class M, int C, bool FINAL, class Loader>
 __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ out_tile,
                                           unsigned char* smem) {

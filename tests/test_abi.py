@@ -1,6 +1,7 @@
 """The C ABI (CPU only): the library loads, exports every symbol that
 include/hc.h declares, sizes its workspaces, and rejects bad arguments on the
 host before any CUDA call (fake device addresses are never dereferenced)."""
+import ctypes
 import os
 import re
 
@@ -32,6 +33,27 @@ def test_every_declared_symbol_exported(L):
     assert _lib.missing_symbols() == []
 
 
+def test_default_schedule_table(L):
+    """hc_set_default_schedule changes what hc_convolve and hc_workspace_size
+    use for one (D, dtype); NULL restores the built-in choice."""
+    got = _lib.hc_schedule()
+    assert L.hc_get_default_schedule(20, _lib.HC_INT64, ctypes.byref(got)) == 0
+    assert got.kind == _lib.HC_SCHED_CHUNKED
+    builtin = L.hc_workspace_size(20, _lib.HC_INT64)
+    s = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 6, 16)
+    assert L.hc_set_default_schedule(20, _lib.HC_INT64, ctypes.byref(s)) == 0
+    try:
+        assert L.hc_get_default_schedule(20, _lib.HC_INT64, ctypes.byref(got)) == 0
+        assert got.as_dict() == {"kind": 1, "c": 8, "k": 6, "cols": 16}
+        assert L.hc_workspace_size(20, _lib.HC_INT64) == \
+            L.hc_workspace_size_schedule(20, _lib.HC_INT64, ctypes.byref(s))
+        assert L.hc_workspace_size(19, _lib.HC_INT64) != 0  # other entries untouched
+    finally:
+        assert L.hc_set_default_schedule(20, _lib.HC_INT64, None) == 0
+    assert L.hc_workspace_size(20, _lib.HC_INT64) == builtin
+    assert L.hc_autotune_workspace_size(20, _lib.HC_INT64) >= builtin
+
+
 def test_status_strings(L):
     for s in range(8):
         assert L.hc_status_string(s).decode().startswith("HC_")
@@ -42,11 +64,18 @@ def test_workspace_sizes(L):
     assert L.hc_workspace_size(-1, 0) == 0
     assert L.hc_workspace_size(_lib.HC_MAX_D + 1, 0) == 0
     assert L.hc_workspace_size(5, 9) == 0
-    # D <= tile axes: a header only
-    assert L.hc_workspace_size(8, _lib.HC_INT64) == 256
-    # D = 20 int64: two evaluated operands of 3^12 * 2^8 int64 and ping-pong buffers
+    # default (chunked) schedule: a single chunk with at most 3 middle axes
+    # needs only the status header and two counters
+    assert L.hc_workspace_size(8, _lib.HC_INT64) == 512
+    assert L.hc_workspace_size(11, _lib.HC_INT64) == 512
+    # D = 20 int64: 3^6 chunks of 14 axes; the operands evaluated on the 6
+    # outer and the first 3 middle axes, [3^9][2^11] int64 each
     ws = L.hc_workspace_size(20, _lib.HC_INT64)
-    assert ws >= 2 * 3 ** 12 * 2 ** 8 * 8
+    assert ws >= 2 * 3 ** 9 * 2 ** 11 * 8
+    # whole-array-pass schedule: operands evaluated on the 12 outer axes
+    s = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 6, 0)
+    assert L.hc_workspace_size_schedule(20, _lib.HC_INT64, ctypes.byref(s)) >= \
+        2 * 3 ** 12 * 2 ** 8 * 8
     # mixed precision keeps a float-float copy of the 3^D intermediate
     assert L.hc_workspace_size(16, _lib.HC_FP32_MIXED) >= 3 ** 16 * 8
 
@@ -77,7 +106,11 @@ def test_argument_errors_caught_on_host(L):
     # workspace overlapping the output
     assert conv(x, y, zz, 20, _lib.HC_INT64, zz, big, None) == _lib.HC_ERR_ALIAS
     # explicit schedules out of range
-    cfg = L.hc_convolve_config
-    assert cfg(x, y, z, 10, _lib.HC_INT64, 9, 0, ws, size, None) == _lib.HC_ERR_ARG
-    assert cfg(x, y, z, 10, _lib.HC_INT64, 0, 7, ws, size, None) == _lib.HC_ERR_ARG
+    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (3, 0, 0, 0), (1, 0, 0, 12), (-1, 0, 0, 0)]:
+        s = _lib.hc_schedule(*bad)
+        assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, ctypes.byref(s), ws, size,
+                                      None) == _lib.HC_ERR_ARG
+        assert L.hc_set_default_schedule(10, _lib.HC_INT64, ctypes.byref(s)) == _lib.HC_ERR_ARG
+    assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, None, ws, size, None) == \
+        _lib.HC_ERR_ARG
     assert L.hc_device_status(None, None) == _lib.HC_ERR_ARG

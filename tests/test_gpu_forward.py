@@ -101,6 +101,34 @@ def test_fp_every_schedule(hc, dt, c, kmax):
     assert_bit_equal(gpu_conv(hc, x, y, c=c, kmax=kmax), oracle.convolve(x, y, threads=8))
 
 
+@pytest.mark.parametrize("c", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("m", [1, 3, 4, 6])
+def test_int64_chunked_every_schedule(hc, c, m):
+    """Chunked schedule: chunks of c + m axes in one persistent launch, the
+    D - c - m outer axes by whole-array passes (D = 13 gives up to 9 outer
+    axes: two evaluation and two interpolation passes)."""
+    D = 13
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=100 * c + m)
+    assert_bit_equal(gpu_conv(hc, x, y, c=c, m=m), oracle.convolve(x, y))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("c,m", [(2, 1), (4, 5), (8, 6), (9, 6), (9, 2)])
+def test_fp_chunked_schedules(hc, dt, c, m):
+    if c == 9 and dt != np.float32:
+        pytest.skip("9-axis tiles are float32 only")
+    D = 14
+    x, y = inputs.normal_pair(D, seed=c + 10 * m, dtype=dt)
+    assert_bit_equal(gpu_conv(hc, x, y, c=c, m=m), oracle.convolve(x, y, threads=8))
+
+
+@pytest.mark.parametrize("c,m", [(3, 2), (8, 4), (8, 6)])
+def test_mixed_chunked_schedules(hc, c, m):
+    D = 13
+    x, y = inputs.uniform01_pair(D, seed=c + m)
+    assert_bit_equal(gpu_conv(hc, x, y, mixed=True, c=c, m=m), oracle.convolve_mixed(x, y))
+
+
 def test_mixed_every_schedule(hc):
     D = 12
     x, y = inputs.uniform01_pair(D, seed=5)

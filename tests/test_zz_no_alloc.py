@@ -49,9 +49,9 @@ def _no_alloc(L, x, y, D, code, tdtype):
 
 CASES = [
     # (code, torch dtype, D of the first call, D of the second call)
-    (_lib.HC_INT64, torch.int64, 15, 12),
+    (_lib.HC_INT64, torch.int64, 16, 12),
     (_lib.HC_FP64, torch.float64, 13, 15),
-    (_lib.HC_FP32, torch.float32, 16, 11),
+    (_lib.HC_FP32, torch.float32, 17, 11),
     (_lib.HC_FP32_MIXED, torch.float32, 13, 12),
 ]
 
@@ -79,8 +79,10 @@ def test_no_alloc_matches_hc_convolve_on_two_calls_in_a_row(L, code, tdtype, D1,
 
 
 def test_no_alloc_refuses_problems_beyond_its_array(L):
-    D = 16  # int64 needs about 37 MiB of workspace, more than the 16 MiB array
-    assert L.hc_workspace_size(D, _lib.HC_INT64) > 16 << 20
+    D = 18  # int64 needs about 114 MiB of workspace, more than the 16 MiB array
+    import ctypes
+    builtin = _lib.hc_schedule(_lib.HC_SCHED_CHUNKED, 0, 0, 0)
+    assert L.hc_workspace_size_schedule(D, _lib.HC_INT64, ctypes.byref(builtin)) > 16 << 20
     x = torch.zeros(1 << D, dtype=torch.int64, device=DEV)
     z = torch.empty(3 ** D, dtype=torch.int64, device=DEV)
     s = L.hc_convolve_noalloc(x.data_ptr(), x.data_ptr(), z.data_ptr(), D, _lib.HC_INT64,
