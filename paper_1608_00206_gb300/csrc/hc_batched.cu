@@ -59,7 +59,7 @@ static hc_status build_batch(const hc_instance* inst, int n, hc_dtype dt, BatchP
   if (es == 0) return HC_ERR_DTYPE;
   const int cmax = batch_cmax(dt);
   const size_t wsz = (dt == HC_FP32_MIXED) ? 8 : es;
-  const int L = wsz == 4 ? 32 : 16;
+  const int L = kPersistCols;
   BatchPlan p;
   memset(&p, 0, sizeof(p));
   p.dtype = dt;
@@ -85,7 +85,7 @@ static hc_status build_batch(const hc_instance* inst, int n, hc_dtype dt, BatchP
     d.n_tiles = (int)pow3z(d.m);
     if (d.m > 0) {
       const long long coltiles = ((long long)pow3z(d.C) + L - 1) / L;
-      long long cpt = 8192 / ((long long)pow3z(d.m) * L);
+      long long cpt = 32768 / ((long long)pow3z(d.m) * L);
       if (cpt < 1) cpt = 1;
       d.cpt = (int)cpt;
       d.n_cols = (int)((coltiles + cpt - 1) / cpt);
@@ -101,7 +101,7 @@ static hc_status build_batch(const hc_instance* inst, int n, hc_dtype dt, BatchP
       wbytes = align_up(wbytes + 8 * pow3z(q.D), 256);
     }
     size_t s = d.C > 0 ? tile_smem_bytes(dt, d.C) : 0;
-    const size_t ism = d.m >= 4 ? wsz * pow3z(d.m) * L : 0;
+    const size_t ism = d.m >= 4 ? 2 * wsz * pow3z(d.m) * L : 0;
     if (ism > s) s = ism;
     if (s > smem) smem = s;
     if (descs) (*descs)[i] = d;

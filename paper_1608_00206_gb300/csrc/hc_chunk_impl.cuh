@@ -12,7 +12,7 @@
 namespace hc {
 
 template <class M, int C, bool FIN>
-__global__ void __launch_bounds__(256) chunk_kernel(UniformUnits uu, long long total,
+__global__ void __launch_bounds__(256, (sizeof(typename M::W) == 4 ? 3 : 2)) chunk_kernel(UniformUnits uu, long long total,
                                                     unsigned long long* counters, WsHeader* hdr) {
   extern __shared__ __align__(16) unsigned char smem[];
   persistent_loop<M, C, true, FIN>(nullptr, nullptr, uu, total, counters, hdr, smem);

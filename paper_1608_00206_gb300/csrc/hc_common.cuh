@@ -30,11 +30,21 @@ __host__ __device__ inline long long pow3_dev(int k) {
   return r;
 }
 
+// 3^k for small k (k <= 19), in 32-bit arithmetic.
+__host__ __device__ inline int pow3i(int k) {
+  int r = 1;
+  for (int i = 0; i < k; ++i) r *= 3;
+  return r;
+}
+
 inline size_t pow3z(int k) {
   size_t r = 1;
   for (int i = 0; i < k; ++i) r *= 3;
   return r;
 }
+
+// Columns per column tile in the persistent ticket engine (host and device).
+constexpr int kPersistCols = 8;
 
 // A float-float value h + l (|l| <= ulp(h)/2 after renormalisation).
 struct __align__(8) ffv {

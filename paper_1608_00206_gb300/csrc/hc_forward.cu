@@ -261,12 +261,12 @@ ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
     }
     p.n_interp = np;
   }
-  p.L = wsz == 4 ? 32 : 16;
+  p.L = kPersistCols;
   p.units = (long long)pow3z(p.ap);
   p.n_tiles = (int)pow3z(p.m);
   if (p.m > 0) {
     const long long coltiles = ((long long)pow3z(C) + p.L - 1) / p.L;
-    long long cpt = 8192 / ((long long)pow3z(p.m) * p.L);
+    long long cpt = 32768 / ((long long)pow3z(p.m) * p.L);
     if (cpt < 1) cpt = 1;
     p.cpt = (int)cpt;
     p.n_cols = (int)((coltiles + cpt - 1) / cpt);
@@ -277,7 +277,7 @@ ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
   p.per_unit = p.n_tiles + p.n_cols;
   p.total = p.units * p.per_unit;
   size_t smem = tile_smem_bytes(dt, C);
-  const size_t ismem = p.m >= 4 ? wsz * pow3z(p.m) * p.L : 0;
+  const size_t ismem = p.m >= 4 ? 2 * wsz * pow3z(p.m) * p.L : 0;  // two column tiles in flight
   p.smem = smem > ismem ? smem : ismem;
   size_t off = kWsHeader;
   auto take = [&](size_t bytes) {

@@ -87,18 +87,41 @@ inline cudaError_t launch_eval(int K, const typename M::In* sx, const typename M
 // array; a CTA tile is all 3^k rows of L consecutive columns of one h.
 // src and dst may be the same array (every tile reads its elements before
 // writing any; tiles are disjoint).
+// Whether the pass double-buffers its tiles: only when two buffers still let
+// two CTAs share an SM (otherwise the lost occupancy costs more than the
+// overlap gains; measured on GB300).
+template <class M, int K1, int K2, int L>
+struct InterpPipe {
+  static constexpr size_t kBuf = sizeof(typename M::W) * (size_t)p3(K1 + K2) * L;
+  static constexpr bool kOn = K1 > 0 && 2 * kBuf <= 113 * 1024;
+  static constexpr size_t kSmem = K1 == 0 ? 0 : (kOn ? 2 * kBuf : kBuf);
+};
+
 template <class M, int K1, int K2, int L, bool FINAL>
 __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256) interp_pass_kernel(const typename M::W* src, void* dst_,
                                                           long long hi, long long lo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long ctiles = (lo + L - 1) / L;
   const long long ntiles = hi * ctiles;
+  if constexpr (InterpPipe<M, K1, K2, L>::kOn) {
+    // this CTA's tiles blockIdx.x, blockIdx.x + gridDim.x, ... double-buffered
+    const long long first = blockIdx.x, step = gridDim.x;
+    const int n = first < ntiles ? (int)((ntiles - 1 - first) / step + 1) : 0;
+    auto tile = [&](int i, long long& base, long long& l0) {
+      const long long t = first + (long long)i * step;
+      const long long h = t / ctiles;
+      l0 = (t - h * ctiles) * L;
+      base = h * p3(K1 + K2) * lo + l0;
+    };
+    interp_tiles_pipelined<M, K1, K2, L, FINAL>(src, dst_, lo, n, tile, smem);
+  } else {
 #pragma unroll 1
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long h = tile / ctiles;
-    const long long l0 = (tile - h * ctiles) * L;
-    interp_tile_body<M, K1, K2, L, FINAL, false>(src, dst_, h * p3(K1 + K2) * lo + l0, l0, lo,
-                                                 smem);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const long long h = tile / ctiles;
+      const long long l0 = (tile - h * ctiles) * L;
+      interp_tile_body<M, K1, K2, L, FINAL, false>(src, dst_, h * p3(K1 + K2) * lo + l0, l0, lo,
+                                                   smem);
+    }
   }
 }
 
@@ -115,7 +138,7 @@ template <class M, int K1, int K2, int L, bool FINAL>
 inline cudaError_t launch_interp_kl(const typename M::W* src, void* dst, long long hi,
                                     long long lo, cudaStream_t st) {
   constexpr int LT = K1 > 0 ? L : 256;
-  const size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
+  const size_t smem = InterpPipe<M, K1, K2, LT>::kSmem;
   auto k = interp_pass_kernel<M, K1, K2, LT, FINAL>;
   ProfileScope prof(st, "interp_pass");
   cudaError_t e = prep_kernel(k, smem);

@@ -68,51 +68,69 @@ constexpr unsigned long long kPoison = 1ull << 63;
 // the m axes with digit 1 are summed as a pairwise tree whose first level
 // pairs the outermost of them (the recursion evaluates axis 1 before axis 2,
 // so its sums nest that way).  Leaves are loaded in blocks of 2^min(m,3)
-// independent loads (one memory round trip per block); a block is a subtree
-// of the three outermost digit-1 axes, and blocks are combined in order.
+// independent loads (one memory round trip per block; with m <= 3 the whole
+// value is one loop-free block); a block is a subtree of the three outermost
+// digit-1 axes, and blocks are combined in order.
 template <class M>
 struct OtfLoader {
   typedef typename M::In In;
   const In* x;
   const In* y;
-  long long base;       // fixed bits, as a flat offset
-  long long stride[6];  // flat offsets of the digit-1 axes, outermost first
-  int m;
-  __device__ __forceinline__ In operator()(int op, int i) const {
-    const In* s = (op ? y : x) + base + i;
-    if (m == 0) return s[0];
-    const int mb = m < 3 ? m : 3;
-    long long lo_off[8];
+  long long base;  // fixed bits, as a flat offset
+  int m;           // digit-1 axes added so far
+  int off[8];      // leaf offsets within a block: the three outermost digit-1 axes
+  int hoff[8];     // block offsets: the digit-1 axes beyond the third
+
+  __device__ __forceinline__ void init(const In* x_, const In* y_, long long base_) {
+    x = x_;
+    y = y_;
+    base = base_;
+    m = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) off[j] = hoff[j] = 0;
+  }
+
+  // Next digit-1 axis (axis order), `bit` its flat offset (< 2^31: a unit
+  // row has at most 2^15 elements).  All indices are static after unrolling,
+  // so the loader stays in registers.
+  __device__ __forceinline__ void add_axis(int bit) {
+    const int q = m++;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      long long o = 0;
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (q < mb && ((j >> q) & 1)) o += stride[q];
-      lo_off[j] = o;
+      if (q < 3) {
+        if ((j >> q) & 1) off[j] += bit;
+      } else {
+        if ((j >> (q - 3)) & 1) hoff[j] += bit;
+      }
     }
-    const int nblocks = 1 << (m - mb);
+  }
+
+  // The pairwise tree over one block of 2^mb leaves.
+  __device__ __forceinline__ In block_sum(const In* s, int mb) const {
+    In v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j < (1 << mb)) v[j] = s[off[j]];
+    if (mb == 0) return v[0];
+    if (mb == 1) return M::add(v[0], v[1]);
+    if (mb == 2) return M::add(M::add(v[0], v[1]), M::add(v[2], v[3]));
+    return M::add(M::add(M::add(v[0], v[1]), M::add(v[2], v[3])),
+                  M::add(M::add(v[4], v[5]), M::add(v[6], v[7])));
+  }
+
+  __device__ __forceinline__ In operator()(int op, int i) const {
+    const In* s = (op ? y : x) + base + i;
+    if (m <= 3) return block_sum(s, m);  // one block: no loop, loads issue together
+    const int nblocks = 1 << (m - 3);
     In stack[4];
     int sp = 0;
 #pragma unroll 1
     for (int blk = 0; blk < nblocks; ++blk) {
-      long long hi = 0;
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (q + 3 < m && ((blk >> q) & 1)) hi += stride[q + 3];
-      In v[8];
+      int h = 0;
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        if (j < (1 << mb)) v[j] = s[hi + lo_off[j]];
-      In r;
-      if (mb == 1) {
-        r = M::add(v[0], v[1]);
-      } else if (mb == 2) {
-        r = M::add(M::add(v[0], v[1]), M::add(v[2], v[3]));
-      } else {
-        r = M::add(M::add(M::add(v[0], v[1]), M::add(v[2], v[3])),
-                   M::add(M::add(v[4], v[5]), M::add(v[6], v[7])));
-      }
+        if (j == blk) h = hoff[j];
+      In r = block_sum(s + h, 3);
 #pragma unroll 1
       for (int t = blk; t & 1; t >>= 1) r = M::add(stack[--sp], r);
       stack[sp++] = r;
@@ -123,7 +141,7 @@ struct OtfLoader {
 
 template <class M>
 struct PersistCols {
-  static constexpr int L = sizeof(typename M::W) == 4 ? 32 : 16;
+  static constexpr int L = kPersistCols;
 };
 
 template <class M>
@@ -152,22 +170,6 @@ __device__ __forceinline__ void tile_any_c(int C, const OtfLoader<M>& ld, void* 
     case 9:
       if constexpr (sizeof(typename M::W) == 4) tile_body<M, 9, FINAL>(ld, out, smem);
       break;
-  }
-}
-
-// Interpolation of the m middle axes over one column tile [l0, l0 + L) of a
-// [3^m][lo] array (src and dst offset to the unit).
-template <class M, bool FIN>
-__device__ __forceinline__ void cols_interp(int m, const typename M::W* src, void* dst,
-                                            long long l0, long long lo, unsigned char* smem) {
-  constexpr int L = PersistCols<M>::L;
-  switch (m) {
-    case 1: interp_tile_body<M, 0, 1, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
-    case 2: interp_tile_body<M, 0, 2, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
-    case 3: interp_tile_body<M, 0, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
-    case 4: interp_tile_body<M, 1, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
-    case 5: interp_tile_body<M, 2, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
-    case 6: interp_tile_body<M, 3, 3, L, FIN, true>(src, dst, l0, l0, lo, smem); break;
   }
 }
 
@@ -211,20 +213,24 @@ __device__ __forceinline__ void cols_small(int m, const typename M::W* src, void
 // unit earlier, so it rarely waits; two units are in L2 at a time.
 __device__ __forceinline__ void uniform_ticket(long long t, const UniformUnits& uu, int& u,
                                                long long& local) {
-  const long long nt = uu.n_tiles, per = uu.per_unit;
-  if (t < nt) {
+  // Ticket counts stay below 2^31 (at most 3^10 units of at most ~1600
+  // tickets), so the decoding runs in 32-bit arithmetic.
+  const unsigned nt = (unsigned)uu.n_tiles, per = (unsigned)uu.per_unit;
+  const unsigned tt = (unsigned)t;
+  if (tt < nt) {
     u = 0;
-    local = t;
+    local = tt;
     return;
   }
-  const long long tp = t - nt;
-  if (tp < (long long)(uu.units - 1) * per) {
-    const long long b = tp / per, r = tp - b * per;
+  const unsigned tp = tt - nt;
+  const unsigned body = (unsigned)(uu.units - 1) * per;
+  if (tp < body) {
+    const unsigned b = tp / per, r = tp - b * per;
     u = (int)(r < nt ? b + 1 : b);
     local = r;  // a column's local index is n_tiles + its column number = r
   } else {
     u = uu.units - 1;
-    local = nt + (tp - (long long)(uu.units - 1) * per);
+    local = nt + (tp - body);
   }
 }
 
@@ -298,22 +304,27 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
       if (tid == 0) next = (long long)atomicAdd(&counters[0], 1ull);  // tiles never wait
       // ---- tile at middle digits alpha = local (the unit's axis 1 most
       // significant): m_pre pre-evaluated digits (a row index), then the
-      // m - m_pre on-the-fly ones
+      // m - m_pre on-the-fly ones.  32-bit arithmetic with constant divisors
+      // only: this runs in every thread of every tile.
       const int m_otf = d.m - d.m_pre;
-      const long long p3otf = pow3_dev(m_otf);
+      const int p3otf = pow3i(m_otf);
+      const int loc = (int)local;  // < 3^m <= 729
+      const int pre_row = loc / p3otf;
+      int rem = loc - pre_row * p3otf;
+      int dg[6];
+#pragma unroll
+      for (int q = 5; q >= 0; --q) {
+        dg[q] = rem % 3;
+        rem /= 3;
+      }
       OtfLoader<M> ld;
-      ld.x = (const In*)d.x;
-      ld.y = (const In*)d.y;
-      ld.base = (local / p3otf) << (C + m_otf);
-      ld.m = 0;
-      long long w3 = p3otf / 3;
-      const long long otf = local % p3otf;
-      for (int q = 0; q < m_otf; ++q) {
-        const int digit = (int)((otf / w3) % 3);
-        w3 /= 3;
-        const long long bit = (long long)1 << (C + (m_otf - 1 - q));
-        if (digit == 2) ld.base += bit;
-        if (digit == 1) ld.stride[ld.m++] = bit;
+      ld.init((const In*)d.x, (const In*)d.y, (long long)pre_row << (C + m_otf));
+#pragma unroll
+      for (int q6 = 0; q6 < 6; ++q6) {
+        if (q6 < 6 - m_otf) continue;
+        const int bit = 1 << (C + 5 - q6);  // axis q6 - (6 - m_otf) of the m_otf
+        if (dg[q6] == 2) ld.base += bit;
+        if (dg[q6] == 1) ld.add_axis(bit);
       }
       if (d.m == 0) {
         if constexpr (CT > 0)
@@ -321,14 +332,15 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
         else
           tile_any_c<M, true>(C, ld, (Out*)d.z, smem);
       } else {
-        W* out = (W*)d.w + local * pow3_dev(C);
+        W* out = (W*)d.w + (long long)loc * (CT > 0 ? p3(CT > 0 ? CT : 1) : pow3i(C));
         if constexpr (CT > 0)
           tile_body<M, (CT > 0 ? CT : 1), false>(ld, out, smem);
         else
           tile_any_c<M, false>(C, ld, out, smem);
-        // release: the barrier orders every thread's stores before thread 0's
-        // fence, which orders them before the counter increment
-        __syncthreads();
+        // release: a barrier (the tile body's last one for tiles of more than
+        // three axes) orders every thread's stores before thread 0's fence,
+        // which orders them before the counter increment
+        if (C <= 3) __syncthreads();
         if (tid == 0) {
           __threadfence();
           atomicAdd(&counters[1 + u], 1ull);
@@ -337,11 +349,12 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
     } else {
       // ---- column ticket: interpolate the m middle axes
       if (tid == 0) {
-        volatile unsigned long long* done = &counters[1 + u];
+        const unsigned long long* done = &counters[1 + u];
         unsigned long long spins = 0;
         int ok = 1;
         for (;;) {
-          const unsigned long long v = *done;
+          unsigned long long v;  // acquire: the unit's tile outputs are visible after it
+          asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(done) : "memory");
           if (v & kPoison) {
             ok = 0;
             break;
@@ -356,22 +369,28 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
             break;
           }
         }
-        __threadfence();
         s_ok[it] = ok;
         next = (long long)atomicAdd(&counters[0], 1ull);  // the wait is over
       }
       __syncthreads();
       if (s_ok[it]) {
         constexpr int L = PersistCols<M>::L;
-        const long long lo = pow3_dev(C);
+        const long long lo = CT > 0 ? p3(CT > 0 ? CT : 1) : pow3i(C);
         const long long c0 = (local - d.n_tiles) * d.cpt * L;
         const long long c1 = (c0 + (long long)d.cpt * L < lo) ? c0 + (long long)d.cpt * L : lo;
         if (d.m <= 3) {
           cols_small<M, FIN>(d.m, (const W*)d.w, d.z, c0, c1, lo);
         } else {
-#pragma unroll 1
-          for (long long l0 = c0; l0 < c1; l0 += L)
-            cols_interp<M, FIN>(d.m, (const W*)d.w, d.z, l0, lo, smem);
+          const int n = (int)((c1 - c0 + L - 1) / L);
+          auto tile = [&](int i, long long& base, long long& l0) {
+            l0 = c0 + (long long)i * L;
+            base = l0;
+          };
+          switch (d.m) {
+            case 4: interp_tiles_pipelined<M, 1, 3, L, FIN>((const W*)d.w, d.z, lo, n, tile, smem); break;
+            case 5: interp_tiles_pipelined<M, 2, 3, L, FIN>((const W*)d.w, d.z, lo, n, tile, smem); break;
+            case 6: interp_tiles_pipelined<M, 3, 3, L, FIN>((const W*)d.w, d.z, lo, n, tile, smem); break;
+          }
         }
       }
     }

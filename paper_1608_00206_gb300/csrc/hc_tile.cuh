@@ -6,6 +6,23 @@
 
 namespace hc {
 
+// Asynchronous global -> shared copies (cp.async, sm_80+), 4 or 8 bytes.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <bool CG, class T>
 __device__ __forceinline__ T ldw(const T* p) {
   if constexpr (CG) {
@@ -310,6 +327,84 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
       }
       __syncthreads();  // shared tile reused by the caller's next tile
     }
+  }
+}
+
+// Pipelined interpolation of k = K1 + K2 axes (K1 > 0) over a sequence of
+// column tiles.  Tile i is rows base_i + j * lo (j < 3^k), columns
+// l0_i + [0, L) clipped to lo.  Its elements are copied into shared buffer
+// i % 2 with cp.async while tile i - 1 is being interpolated; round 1
+// interpolates the inner K2 axes in place in shared memory, round 2 the outer
+// K1 axes from shared memory to dst.  smem: 2 * 3^k * L W elements.
+// `tile(i, base, l0)` yields the position of tile i; n tiles in all.
+template <class M, int K1, int K2, int L, bool FINAL, class TileFn>
+__device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src, void* dst_,
+                                                       long long lo, int n, const TileFn& tile,
+                                                       unsigned char* smem) {
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  constexpr int ROWS = p3(K1 + K2);
+  constexpr int NE = ROWS * L;
+  W* buf0 = reinterpret_cast<W*>(smem);
+  W* buf1 = buf0 + NE;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto prefetch = [&](int i, W* b) {
+    long long base, l0;
+    tile(i, base, l0);
+#pragma unroll 1
+    for (int e = tid; e < NE; e += nt) {
+      const int row = e / L, l = e - row * L;
+      if (l0 + l < lo) cp_async<sizeof(W)>(b + e, src + base + (long long)row * lo + l);
+    }
+    cp_async_commit();
+  };
+  if (n > 0) prefetch(0, buf0);
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    W* b = (i & 1) ? buf1 : buf0;
+    if (i + 1 < n) {
+      prefetch(i + 1, (i & 1) ? buf0 : buf1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // tile i's elements are in b
+    long long base, l0;
+    tile(i, base, l0);
+    // round 1: inner K2 axes, in place
+#pragma unroll 1
+    for (int p = tid; p < p3(K1) * L; p += nt) {
+      const int o = p / L, l = p - o * L;
+      if (l0 + l >= lo) continue;
+      W v[p3(K2)];
+#pragma unroll
+      for (int j = 0; j < p3(K2); ++j) v[j] = b[(o * p3(K2) + j) * L + l];
+      interp_pencil<M, K2>(v);
+#pragma unroll
+      for (int j = 0; j < p3(K2); ++j) b[(o * p3(K2) + j) * L + l] = v[j];
+    }
+    __syncthreads();
+    // round 2: outer K1 axes, shared -> global
+#pragma unroll 1
+    for (int p = tid; p < p3(K2) * L; p += nt) {
+      const int r = p / L, l = p - r * L;
+      if (l0 + l >= lo) continue;
+      W v[p3(K1)];
+#pragma unroll
+      for (int j = 0; j < p3(K1); ++j) v[j] = b[(j * p3(K2) + r) * L + l];
+      interp_pencil<M, K1>(v);
+      if constexpr (FINAL) {
+        Out* d = reinterpret_cast<Out*>(dst_);
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j)
+          d[base + (long long)(j * p3(K2) + r) * lo + l] = M::out(v[j]);
+      } else {
+        W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) d[base + (long long)(j * p3(K2) + r) * lo + l] = v[j];
+      }
+    }
+    __syncthreads();  // b is refilled two tiles later
   }
 }
 
