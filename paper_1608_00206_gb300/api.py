@@ -66,6 +66,9 @@ def workspace_size(D: int, dtype: torch.dtype = torch.float32, mixed: bool = Fal
     code = _code(dtype, mixed)
     s = _schedule(c, kmax, m, cols)
     if s is None:
+        # the default schedule is the tuned one once the table is installed
+        if torch.cuda.is_available():
+            tuning.ensure_installed(torch.device("cuda", torch.cuda.current_device()))
         return int(_lib.lib().hc_workspace_size(D, code))
     return int(_lib.lib().hc_workspace_size_schedule(D, code, ctypes.byref(s)))
 

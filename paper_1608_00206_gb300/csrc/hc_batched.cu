@@ -80,7 +80,10 @@ static hc_status build_batch(const hc_instance* inst, int n, hc_dtype dt, BatchP
     d.y = q.y;
     d.z = q.z;
     d.w = q.z;
-    d.C = q.D < cmax ? q.D : cmax;
+    // 8-axis tiles keep the persistent kernel at several CTAs per SM (a
+    // 9-axis float32 tile needs 126 KB of shared memory); 9 only when D = 15.
+    const int ctile = q.D > 8 + 6 ? cmax : 8;
+    d.C = q.D < ctile ? q.D : ctile;
     d.m = q.D - d.C;
     d.n_tiles = (int)pow3z(d.m);
     if (d.m > 0) {

@@ -37,6 +37,14 @@ struct RowLoader {
   __device__ __forceinline__ In operator()(int op, int i) const { return op ? y[i] : x[i]; }
 };
 
+// The tile's input rows come from a double buffer that cp.async fills with
+// the next tile's rows while the current tile is being computed.
+template <class M, int C>
+struct TileRows {
+  static constexpr size_t kOff = (TileSmem<M, C>::bytes + 15) / 16 * 16;
+  static constexpr size_t bytes = kOff + 2 * 2 * sizeof(typename M::In) * (size_t)p2(C);
+};
+
 template <class M, int C, bool FINAL>
 __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __restrict__ X,
                                                         const typename M::In* __restrict__ Y,
@@ -44,10 +52,29 @@ __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __
   typedef typename M::In In;
   typedef typename std::conditional<FINAL, typename M::Out, typename M::W>::type O;
   extern __shared__ __align__(16) unsigned char smem[];
+  In* rows = reinterpret_cast<In*>(smem + TileRows<M, C>::kOff);  // [buffer][operand][2^C]
+  auto prefetch = [&](long long t, int b) {
 #pragma unroll 1
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    RowLoader<In> ld{X + t * p2(C), Y + t * p2(C)};
+    for (int e = threadIdx.x; e < 2 * p2(C); e += blockDim.x) {
+      const int op = e >> C, i = e & (p2(C) - 1);
+      cp_async<sizeof(In)>(rows + (b * 2 + op) * p2(C) + i, (op ? Y : X) + t * p2(C) + i);
+    }
+    cp_async_commit();
+  };
+  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0);
+  int it = 0;
+#pragma unroll 1
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it ^= 1) {
+    if (t + gridDim.x < ntiles) {
+      prefetch(t + gridDim.x, it ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // this tile's rows are in buffer `it`
+    RowLoader<In> ld{rows + (it * 2 + 0) * p2(C), rows + (it * 2 + 1) * p2(C)};
     tile_body<M, C, FINAL>(ld, reinterpret_cast<O*>(out_) + t * p3(C), smem);
+    if constexpr (TileShape<C>::G == 1) __syncthreads();  // buffer reuse (larger tiles end with one)
   }
 }
 
@@ -66,12 +93,12 @@ static int max_tile_axes() {
   return sizeof(typename M::W) == 4 ? 9 : 8;
 }
 
-static int threads_for_tile(int C) { return C >= 6 ? 256 : (C >= 4 ? 128 : 32); }
+static int threads_for_tile(int C) { return C >= 4 ? 256 : 32; }
 
 template <class M, int C, bool FINAL>
 static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* Y, void* out,
                                  long long ntiles, cudaStream_t st) {
-  const size_t smem = TileSmem<M, C>::bytes;
+  const size_t smem = TileRows<M, C>::bytes;
   auto k = tile_conv_kernel<M, C, FINAL>;
   ProfileScope prof(st, "tile_conv");
   cudaError_t e = prep_kernel(k, smem);

@@ -74,7 +74,13 @@ struct TileSmem {
   static constexpr size_t kLast = sizeof(In) * (size_t)p2(TileShape<C>::gL) * p3(C - TileShape<C>::gL);
   static constexpr size_t kS1 = TileShape<C>::G == 3 ? 2 * sizeof(In) * (size_t)p3(TileShape<C>::g0) * p2(C - TileShape<C>::g0) : 0;
   static_assert(kS1 <= kW, "stage-0 buffer must fit inside the W tile");
-  static constexpr size_t bytes = kW + (TileShape<C>::G >= 2 ? 2 * kLast : 0);
+  // With at most 256 fused pencils (one per thread of a 256-thread CTA) the
+  // fused stage reads all its inputs before any thread writes W, so the
+  // stage buffers live inside the W tile too: [S1 | LastX | LastY | ...].
+  static constexpr bool kAlias =
+      TileShape<C>::G >= 2 && TileShape<C>::nLastPencils <= 256 && kS1 + 2 * kLast <= kW;
+  static constexpr size_t kLastOff = kAlias ? kS1 : kW;
+  static constexpr size_t bytes = kAlias ? kW : kW + (TileShape<C>::G >= 2 ? 2 * kLast : 0);
 };
 
 // Loader: ld(op, i) returns element i of the tile's operand row (op 0 = x,
@@ -115,7 +121,7 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
   typedef typename M::Out Out;
   typedef TileShape<C> S;
   W* Ws = reinterpret_cast<W*>(smem);
-  In* LastX = reinterpret_cast<In*>(smem + TileSmem<M, C>::kW);
+  In* LastX = reinterpret_cast<In*>(smem + TileSmem<M, C>::kLastOff);
   In* LastY = LastX + p2(S::gL) * p3(C - S::gL);
   In* S1 = reinterpret_cast<In*>(smem);  // G == 3 only; aliases the W tile
   const int tid = threadIdx.x;
@@ -192,7 +198,30 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
         __syncthreads();
       }
       // ---- fused stage: evaluate innermost group, multiply, interpolate it.
-      {
+      if constexpr (TileSmem<M, C>::kAlias) {
+        // one pencil per thread; all inputs are read before W is written
+        constexpr int NO = S::nLastPencils;
+        const int o = tid;
+        In a[27], b[27];
+        if (o < NO) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            a[q] = LastX[q * NO + o];
+            b[q] = LastY[q * NO + o];
+          }
+        }
+        __syncthreads();
+        if (o < NO) {
+          eval_pencil<M, 3>(a);
+          eval_pencil<M, 3>(b);
+          W w[27];
+#pragma unroll
+          for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
+          interp_pencil<M, 3>(w);
+#pragma unroll
+          for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
+        }
+      } else {
         constexpr int NO = S::nLastPencils;
         #pragma unroll 1
         for (int o = tid; o < NO; o += nt) {
