@@ -277,3 +277,16 @@ def convolve_batched(xs, ys, outs=None, *, mixed: bool = False, stream=None):
     """One persistent launch over all instances; returns the list of outputs."""
     b = BatchedConv(xs, ys, outs, mixed=mixed, stream=stream)
     return b.launch(stream)
+
+
+def carry_free_convolve(x: torch.Tensor, y: torch.Tensor, **kw) -> torch.Tensor:
+    """1D carry-free convolution of two length-N vectors, N = 2^D (paper,
+    Discussion): z[k] = sum of x[i] * y[j] over the pairs whose bitwise,
+    carry-free sum is k, i.e. the digits of k in base 3 are bit_d(i) + bit_d(j).
+    With bit d of the index as axis d (most significant first) this is exactly
+    the hypercube convolution of the flat vectors: z has 3^D entries, entry k
+    read as D base-3 digits.  Example: i = 7 = (1,1,1), j = 5 = (1,0,1) lands
+    in (2,1,2) = 23."""
+    if x.dim() != 1 or y.dim() != 1:
+        raise ValueError("carry-free convolution takes 1D vectors")
+    return convolve(x, y, **kw).reshape(-1)

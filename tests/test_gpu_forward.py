@@ -247,3 +247,24 @@ def test_stream_ordering(hc):
         z = hc.convolve(xt, yt)
         zc = z.cpu()
     assert np.array_equal(zc.numpy(), oracle.convolve(x, y))
+
+
+def test_carry_free_1d_convolution(hc):
+    """Discussion section: carry-free 1D convolution is the hypercube
+    convolution of the bit-indexed vectors; 7 (+) 5 lands in (2,1,2) = 23, and
+    a random case matches the definition computed digit by digit."""
+    x = torch.zeros(8, dtype=torch.int64, device=DEV)
+    y = torch.zeros(8, dtype=torch.int64, device=DEV)
+    x[7], y[5] = 3, 4
+    z = hc.carry_free_convolve(x, y).cpu().numpy()
+    assert z[23] == 12 and np.count_nonzero(z) == 1
+    N, D = 1 << 11, 11
+    g = np.random.default_rng(5)
+    xs = g.integers(-9, 10, size=N, dtype=np.int64)
+    ys = g.integers(-9, 10, size=N, dtype=np.int64)
+    z = hc.carry_free_convolve(torch.from_numpy(xs).to(DEV), torch.from_numpy(ys).to(DEV))
+    i = np.arange(N)
+    digits = lambda v: sum(((v >> d) & 1) * 3 ** d for d in range(D))  # noqa: E731
+    want = np.zeros(3 ** D, np.int64)
+    np.add.at(want, (digits(i)[:, None] + digits(i)[None, :]).ravel(), np.outer(xs, ys).ravel())
+    assert np.array_equal(z.cpu().numpy(), want)
