@@ -25,68 +25,6 @@
 namespace hc {
 
 // ---------------------------------------------------------------------------
-// KB3: I^T on k = K1 + K2 consecutive axes of [hi][3^k][lo].  Round 1: the
-// outer K1 axes, pencils read straight from global memory (rows
-// j * 3^K2 + r); round 2: the inner K2 axes after a pass through shared
-// memory.  Consecutive threads take consecutive columns.
-template <class M, int K1, int K2, int L>
-__global__ void __launch_bounds__(256) interp_t_pass_kernel(const typename M::W* src,
-                                                            typename M::W* dst, long long hi,
-                                                            long long lo) {
-  typedef typename M::W W;
-  constexpr int K = K1 + K2;
-  constexpr int ROWS = p3(K);
-  extern __shared__ __align__(16) unsigned char smem[];
-  W* T = reinterpret_cast<W*>(smem);
-  const long long ctiles = (lo + L - 1) / L;
-  const long long ntiles = hi * ctiles;
-  const int tid = threadIdx.x, nt = blockDim.x;
-#pragma unroll 1
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long h = tile / ctiles;
-    const long long l0 = (tile - h * ctiles) * L;
-    const long long base = h * ROWS * lo + l0;
-    if constexpr (K1 == 0) {
-#pragma unroll 1
-      for (int l = tid; l < L; l += nt) {
-        if (l0 + l >= lo) continue;
-        W v[p3(K2)];
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) v[j] = src[base + j * lo + l];
-        interp_t_pencil<M, K2>(v);
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) dst[base + j * lo + l] = v[j];
-      }
-    } else {
-#pragma unroll 1
-      for (int p = tid; p < p3(K2) * L; p += nt) {
-        const int r = p / L, l = p - r * L;
-        if (l0 + l >= lo) continue;
-        W v[p3(K1)];
-#pragma unroll
-        for (int j = 0; j < p3(K1); ++j) v[j] = src[base + (long long)(j * p3(K2) + r) * lo + l];
-        interp_t_pencil<M, K1>(v);
-#pragma unroll
-        for (int j = 0; j < p3(K1); ++j) T[(j * p3(K2) + r) * L + l] = v[j];
-      }
-      __syncthreads();
-#pragma unroll 1
-      for (int p = tid; p < p3(K1) * L; p += nt) {
-        const int o = p / L, l = p - o * L;
-        if (l0 + l >= lo) continue;
-        W v[p3(K2)];
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) v[j] = T[(o * p3(K2) + j) * L + l];
-        interp_t_pencil<M, K2>(v);
-#pragma unroll
-        for (int j = 0; j < p3(K2); ++j) dst[base + (long long)(o * p3(K2) + j) * lo + l] = v[j];
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // KB1: E^T on K axes of [hi][3^K][lo] -> [hi][2^K][lo], for Hx and Hy at once.
 template <class M, int K>
 __global__ void __launch_bounds__(256) evalt_pass_kernel(const typename M::W* __restrict__ sx,
@@ -475,35 +413,6 @@ static BwdPlan make_bwd_plan(int D, hc_dtype dt) {
   return p;
 }
 
-template <class M, int K1, int K2>
-static cudaError_t launch_it_k(const typename M::W* src, typename M::W* dst, long long hi,
-                               long long lo, cudaStream_t st) {
-  constexpr int L = sizeof(typename M::W) == 4 ? 32 : 16;
-  const size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
-  auto k = interp_t_pass_kernel<M, K1, K2, L>;
-  ProfileScope prof(st, "interp_t_pass");
-  cudaError_t e = prep_kernel(k, smem);
-  if (e != cudaSuccess) return e;
-  const int threads = K1 > 0 ? 256 : L;
-  const long long ntiles = hi * ((lo + L - 1) / L);
-  k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(src, dst, hi, lo);
-  return cudaGetLastError();
-}
-
-template <class M>
-static cudaError_t launch_it(int k, const typename M::W* src, typename M::W* dst, long long hi,
-                             long long lo, cudaStream_t st) {
-  switch (k) {
-    case 1: return launch_it_k<M, 0, 1>(src, dst, hi, lo, st);
-    case 2: return launch_it_k<M, 0, 2>(src, dst, hi, lo, st);
-    case 3: return launch_it_k<M, 0, 3>(src, dst, hi, lo, st);
-    case 4: return launch_it_k<M, 1, 3>(src, dst, hi, lo, st);
-    case 5: return launch_it_k<M, 2, 3>(src, dst, hi, lo, st);
-    case 6: return launch_it_k<M, 3, 3>(src, dst, hi, lo, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
 template <class M, int K>
 static cudaError_t launch_et_k(const typename M::W* sx, const typename M::W* sy,
                                typename M::W* dx, typename M::W* dy, long long hi, long long lo,
@@ -580,7 +489,7 @@ static cudaError_t run_backward(const BwdPlan& p, const void* dz, const void* x,
     const int d0 = p.it_d0[i], k = p.it_k[i];
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
-    e = launch_it<M>(k, G, Gbuf, hi, lo, st);
+    e = launch_interp<M, false, true>(k, 0, G, Gbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
     G = Gbuf;
   }

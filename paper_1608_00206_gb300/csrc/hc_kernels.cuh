@@ -97,7 +97,7 @@ struct InterpPipe {
   static constexpr size_t kSmem = K1 == 0 ? 0 : (kOn ? 2 * kBuf : kBuf);
 };
 
-template <class M, int K1, int K2, int L, bool FINAL>
+template <class M, int K1, int K2, int L, bool FINAL, bool TR>
 __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256) interp_pass_kernel(const typename M::W* src, void* dst_,
                                                           long long hi, long long lo) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -113,14 +113,14 @@ __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256) in
       l0 = (t - h * ctiles) * L;
       base = h * p3(K1 + K2) * lo + l0;
     };
-    interp_tiles_pipelined<M, K1, K2, L, FINAL>(src, dst_, lo, n, tile, smem);
+    interp_tiles_pipelined<M, K1, K2, L, FINAL, decltype(tile), TR>(src, dst_, lo, n, tile, smem);
   } else {
 #pragma unroll 1
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const long long h = tile / ctiles;
       const long long l0 = (tile - h * ctiles) * L;
-      interp_tile_body<M, K1, K2, L, FINAL, false>(src, dst_, h * p3(K1 + K2) * lo + l0, l0, lo,
-                                                   smem);
+      interp_tile_body<M, K1, K2, L, FINAL, false, TR>(src, dst_, h * p3(K1 + K2) * lo + l0, l0,
+                                                       lo, smem);
     }
   }
 }
@@ -134,13 +134,13 @@ inline int default_cols() {
 // k = K1 + K2 axes per pass; K1 > 0: a CTA of 27 * L threads (one pencil per
 // thread and round) owns an L-column tile; K1 == 0: 256 columns per CTA, one
 // column per thread.
-template <class M, int K1, int K2, int L, bool FINAL>
+template <class M, int K1, int K2, int L, bool FINAL, bool TR>
 inline cudaError_t launch_interp_kl(const typename M::W* src, void* dst, long long hi,
                                     long long lo, cudaStream_t st) {
   constexpr int LT = K1 > 0 ? L : 256;
   const size_t smem = InterpPipe<M, K1, K2, LT>::kSmem;
-  auto k = interp_pass_kernel<M, K1, K2, LT, FINAL>;
-  ProfileScope prof(st, "interp_pass");
+  auto k = interp_pass_kernel<M, K1, K2, LT, FINAL, TR>;
+  ProfileScope prof(st, TR ? "interp_t_pass" : "interp_pass");
   cudaError_t e = prep_kernel(k, smem);
   if (e != cudaSuccess) return e;
   int threads = K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256;
@@ -150,29 +150,31 @@ inline cudaError_t launch_interp_kl(const typename M::W* src, void* dst, long lo
   return cudaGetLastError();
 }
 
-template <class M, int K1, int K2, bool FINAL>
+template <class M, int K1, int K2, bool FINAL, bool TR>
 inline cudaError_t launch_interp_k(int cols, const typename M::W* src, void* dst, long long hi,
                                    long long lo, cudaStream_t st) {
-  if constexpr (K1 == 0) return launch_interp_kl<M, 0, K2, 256, FINAL>(src, dst, hi, lo, st);
+  if constexpr (K1 == 0) return launch_interp_kl<M, 0, K2, 256, FINAL, TR>(src, dst, hi, lo, st);
   switch (cols) {
-    case 8: return launch_interp_kl<M, K1, K2, 8, FINAL>(src, dst, hi, lo, st);
-    case 16: return launch_interp_kl<M, K1, K2, 16, FINAL>(src, dst, hi, lo, st);
-    case 32: return launch_interp_kl<M, K1, K2, 32, FINAL>(src, dst, hi, lo, st);
+    case 8: return launch_interp_kl<M, K1, K2, 8, FINAL, TR>(src, dst, hi, lo, st);
+    case 16: return launch_interp_kl<M, K1, K2, 16, FINAL, TR>(src, dst, hi, lo, st);
+    case 32: return launch_interp_kl<M, K1, K2, 32, FINAL, TR>(src, dst, hi, lo, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <class M, bool FINAL>
+// Interpolation (TR = false) or its transpose (TR = true) of k consecutive
+// axes of a [hi][3^k][lo] array, src -> dst (may be the same array).
+template <class M, bool FINAL, bool TR = false>
 inline cudaError_t launch_interp(int k, int cols, const typename M::W* src, void* dst,
                                  long long hi, long long lo, cudaStream_t st) {
   if (cols <= 0) cols = default_cols<M>();
   switch (k) {
-    case 1: return launch_interp_k<M, 0, 1, FINAL>(cols, src, dst, hi, lo, st);
-    case 2: return launch_interp_k<M, 0, 2, FINAL>(cols, src, dst, hi, lo, st);
-    case 3: return launch_interp_k<M, 0, 3, FINAL>(cols, src, dst, hi, lo, st);
-    case 4: return launch_interp_k<M, 1, 3, FINAL>(cols, src, dst, hi, lo, st);
-    case 5: return launch_interp_k<M, 2, 3, FINAL>(cols, src, dst, hi, lo, st);
-    case 6: return launch_interp_k<M, 3, 3, FINAL>(cols, src, dst, hi, lo, st);
+    case 1: return launch_interp_k<M, 0, 1, FINAL, TR>(cols, src, dst, hi, lo, st);
+    case 2: return launch_interp_k<M, 0, 2, FINAL, TR>(cols, src, dst, hi, lo, st);
+    case 3: return launch_interp_k<M, 0, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
+    case 4: return launch_interp_k<M, 1, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
+    case 5: return launch_interp_k<M, 2, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
+    case 6: return launch_interp_k<M, 3, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -293,7 +293,9 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
 // One tile: rows base + j * lo for j < 3^k, columns l0 + [0, L) clipped to
 // lo (base already includes l0).  CG = read src through L2 only (data
 // written by other CTAs of the same launch).
-template <class M, int K1, int K2, int L, bool FINAL, bool CG>
+// TR: the transposed map I^T (outer K1 axes first, then the inner K2 axes,
+// each pencil transformed outermost axis first) -- the adjoint's pass.
+template <class M, int K1, int K2, int L, bool FINAL, bool CG, bool TR = false>
 __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void* dst_,
                                                  long long base, long long l0, long long lo,
                                                  unsigned char* smem) {
@@ -309,7 +311,10 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
         W v[p3(K2)];
 #pragma unroll
         for (int j = 0; j < p3(K2); ++j) v[j] = ldw<CG>(src + base + j * lo + l);
-        interp_pencil<M, K2>(v);
+        if constexpr (TR)
+          interp_t_pencil<M, K2>(v);
+        else
+          interp_pencil<M, K2>(v);
         if constexpr (FINAL) {
           Out* d = reinterpret_cast<Out*>(dst_);
 #pragma unroll
@@ -320,6 +325,35 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
           for (int j = 0; j < p3(K2); ++j) d[base + j * lo + l] = v[j];
         }
       }
+    } else if constexpr (TR) {
+      // round 1: outer K1 axes (I^T), global -> registers -> shared
+#pragma unroll 1
+      for (int p = tid; p < p3(K2) * L; p += nt) {
+        const int r = p / L, l = p - r * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K1)];
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j)
+          v[j] = ldw<CG>(src + base + (long long)(j * p3(K2) + r) * lo + l);
+        interp_t_pencil<M, K1>(v);
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) T[(j * p3(K2) + r) * L + l] = v[j];
+      }
+      __syncthreads();
+      // round 2: inner K2 axes (I^T), shared -> registers -> global
+#pragma unroll 1
+      for (int p = tid; p < p3(K1) * L; p += nt) {
+        const int o = p / L, l = p - o * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = T[(o * p3(K2) + j) * L + l];
+        interp_t_pencil<M, K2>(v);
+        W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) d[base + (long long)(o * p3(K2) + j) * lo + l] = v[j];
+      }
+      __syncthreads();
     } else {
       // round 1: inner K2 axes, global -> registers -> shared
       #pragma unroll 1
@@ -366,7 +400,7 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
 // interpolates the inner K2 axes in place in shared memory, round 2 the outer
 // K1 axes from shared memory to dst.  smem: 2 * 3^k * L W elements.
 // `tile(i, base, l0)` yields the position of tile i; n tiles in all.
-template <class M, int K1, int K2, int L, bool FINAL, class TileFn>
+template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false>
 __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src, void* dst_,
                                                        long long lo, int n, const TileFn& tile,
                                                        unsigned char* smem) {
@@ -400,6 +434,34 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src,
     __syncthreads();  // tile i's elements are in b
     long long base, l0;
     tile(i, base, l0);
+    if constexpr (TR) {
+      // I^T: round 1 the outer K1 axes in place, round 2 the inner K2 axes
+#pragma unroll 1
+      for (int p = tid; p < p3(K2) * L; p += nt) {
+        const int r = p / L, l = p - r * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K1)];
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) v[j] = b[(j * p3(K2) + r) * L + l];
+        interp_t_pencil<M, K1>(v);
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) b[(j * p3(K2) + r) * L + l] = v[j];
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int p = tid; p < p3(K1) * L; p += nt) {
+        const int o = p / L, l = p - o * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = b[(o * p3(K2) + j) * L + l];
+        interp_t_pencil<M, K2>(v);
+        W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) d[base + (long long)(o * p3(K2) + j) * lo + l] = v[j];
+      }
+      __syncthreads();
+    } else {
     // round 1: inner K2 axes, in place
 #pragma unroll 1
     for (int p = tid; p < p3(K1) * L; p += nt) {
@@ -434,6 +496,7 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src,
       }
     }
     __syncthreads();  // b is refilled two tiles later
+    }
   }
 }
 
