@@ -172,6 +172,7 @@ class Workload:
 
         self.name = name
         self.dev = dev
+        self.sched = {}
         self.hc = hc
         self.torch = torch
         seed = 1000 + rank
@@ -248,7 +249,30 @@ class Workload:
             loss = (self.w * self.hc.hypercube_conv(self.x, self.y)).sum()
             loss.backward()
         else:
-            self.hc.convolve(self.x, self.y, out=self.z, mixed=self.mixed, workspace=self.ws)
+            self.hc.convolve(self.x, self.y, out=self.z, mixed=self.mixed, workspace=self.ws,
+                             **self.sched)
+
+    def schedule_geometry(self):
+        """(kind, C, m, ap, ev) of the schedule the single-instance step runs."""
+        import ctypes
+
+        from paper_1608_00206_gb300 import _lib
+        code = {"d20_int64": 0, "d10_int64": 0, "d16_fp64": 1, "d18_fp32": 2,
+                "d16_mixed": 3}[self.name]
+        cmax = 9 if code == 2 else 8
+        if self.sched:
+            kind = 2 if "m" in self.sched else 1
+            c, k = self.sched.get("c", 0), self.sched.get("m", self.sched.get("kmax", 0))
+        else:
+            s = _lib.hc_schedule()
+            _lib.lib().hc_get_default_schedule(self.D, code, ctypes.byref(s))
+            kind, c, k = s.kind, s.c, s.k
+        C = min(c or cmax, self.D)
+        if kind == 1:
+            return kind, C, 0, self.D - C, self.D - C
+        m = min(self.D - C, k or 6)
+        ap = self.D - C - m
+        return kind, C, m, ap, ap + max(m - 3, 0)
 
     # per-kernel algorithmic bytes (or FP64 operations) per launch
     def kernel_alg(self, kname, launches_per_step):
@@ -257,6 +281,13 @@ class Workload:
             return self.alg_bytes, "hbm"
         s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64") else 4
         sw = 8 if self.name == "d16_mixed" else s
+        if kname == "chunk":
+            kind, C, m, ap, ev = self.schedule_geometry()
+            if self.name == "d16_fp64":
+                tile = 2 * (3 ** C - 2 ** C) + 3 ** C + 2 * C * 3 ** (C - 1)
+                return 3 ** ap * (3 ** m * tile + 2 * m * 3 ** (C + m - 1)), "alu"
+            # read the operands evaluated on ev axes, write the 3^D intermediate once
+            return 2 * 3 ** ev * 2 ** (D - ev) * s + 3 ** D * sw, "hbm"
         if self.name == "d16_fp64":
             return self._fp64_ops(kname, launches_per_step), "alu"
         if kname in ("interp_pass", "interp_t_pass"):
@@ -518,6 +549,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
+    ap.add_argument("--schedule", default=None,
+                    help="force a schedule kind:c:k:cols (kind passes|chunked) instead of the "
+                         "tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
     if args.D is not None and args.workload not in SINGLE:
         ap.error("--D applies to single-instance workloads only")
@@ -548,6 +582,16 @@ def main():
     torch.cuda.set_device(dev)
 
     wl = Workload(args.workload, dev, rank, args.D)
+    if args.schedule:
+        if args.workload not in SINGLE:
+            ap.error("--schedule applies to single-instance workloads only")
+        kind, c, k, cols = args.schedule.split(":")
+        wl.sched = {"c": int(c), "cols": int(cols),
+                    ("m" if kind == "chunked" else "kmax"): int(k)}
+        if kind not in ("passes", "chunked"):
+            ap.error("schedule kind is passes or chunked")
+        nb = wl.hc.workspace_size(wl.D, wl.z.dtype, wl.mixed, **wl.sched)
+        wl.ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
     ms, prof, clk = _time_steps(wl, args.steps, args.warmup, dist)
     value = world * wl.outputs * args.steps / (ms / 1e3)
 
@@ -580,6 +624,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] if args.D is None else
                    f"{WORKLOADS[args.workload]} with D overridden to {args.D}",
+                   "schedule": args.schedule or "tuned default",
                    "name": args.workload, "D": wl.D,
                    "outputs_per_step": wl.outputs, "parallelism": f"replicas{world}",
                    "l2": "working set larger than L2 (129 MB); no flush"
