@@ -25,7 +25,10 @@ static cudaError_t launch_chunk_c(const ChunkPlan& p, const UniformUnits& uu,
   ProfileScope prof(st, "chunk");
   cudaError_t e = prep_kernel(k, p.smem);
   if (e != cudaSuccess) return e;
-  k<<<grid_for(k, 256, p.smem, p.total), 256, p.smem, st>>>(uu, p.total, ctr, hdr);
+  const int grid = grid_for(k, 256, p.smem, p.total);
+  UniformUnits u2 = uu;
+  u2.lag = grid < p.n_tiles ? grid : p.n_tiles;  // one wave of CTAs (see uniform_ticket)
+  k<<<grid, 256, p.smem, st>>>(u2, p.total, ctr, hdr);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct UniformUnits {
   void* z;
   long long in_stride, out_stride, per_unit;
   int C, m, n_tiles, n_cols, cpt, need, m_pre, units;
+  int lag;  // tiles of unit u claimed before the column tickets of unit u - 1
 };
 
 constexpr unsigned long long kSpinLimit = 1ull << 22;  // x >= 256 ns sleeps: ~1 s
@@ -206,16 +207,20 @@ __device__ __forceinline__ void cols_small(int m, const typename M::W* src, void
   }
 }
 
-// Ticket order.  Unit u's tiles come before its column tickets, and the
-// column tickets of unit u come after the tiles of unit u + 1:
-//   tiles(0), tiles(1), cols(0), tiles(2), cols(1), ..., cols(units - 1).
-// By the time a column ticket is claimed its unit's tiles were claimed one
-// unit earlier, so it rarely waits; two units are in L2 at a time.
+// Ticket order.  Unit u's tiles come before its column tickets; the column
+// tickets of unit u - 1 are placed after the first `lag` tiles of unit u:
+//   tiles(0), tiles(1)[0:lag], cols(0), tiles(1)[lag:], tiles(2)[0:lag],
+//   cols(1), tiles(2)[lag:], ..., cols(units - 1).
+// With lag about the number of resident CTAs, unit u - 1's last tiles are
+// finished when its column tickets are claimed (they rarely wait), and only
+// about 1 + lag / n_tiles units' intermediates are live in L2 at a time
+// (two full units did not stay in L2: DRAM traffic doubled).
 __device__ __forceinline__ void uniform_ticket(long long t, const UniformUnits& uu, int& u,
                                                long long& local) {
   // Ticket counts stay below 2^31 (at most 3^10 units of at most ~1600
   // tickets), so the decoding runs in 32-bit arithmetic.
-  const unsigned nt = (unsigned)uu.n_tiles, per = (unsigned)uu.per_unit;
+  const unsigned nt = (unsigned)uu.n_tiles, nc = (unsigned)uu.n_cols;
+  const unsigned per = nt + nc, lag = (unsigned)uu.lag;
   const unsigned tt = (unsigned)t;
   if (tt < nt) {
     u = 0;
@@ -226,8 +231,16 @@ __device__ __forceinline__ void uniform_ticket(long long t, const UniformUnits& 
   const unsigned body = (unsigned)(uu.units - 1) * per;
   if (tp < body) {
     const unsigned b = tp / per, r = tp - b * per;
-    u = (int)(r < nt ? b + 1 : b);
-    local = r;  // a column's local index is n_tiles + its column number = r
+    if (r < lag) {
+      u = (int)b + 1;
+      local = r;
+    } else if (r < lag + nc) {
+      u = (int)b;
+      local = nt + (r - lag);
+    } else {
+      u = (int)b + 1;
+      local = r - nc;
+    }
   } else {
     u = uu.units - 1;
     local = nt + (tp - body);
