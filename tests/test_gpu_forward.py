@@ -173,8 +173,9 @@ def test_d20_int64_full_size(hc):
     """D = 20 int64, values in [-1000, 1000] (the benchmark workload, same
     launch configuration): 3^20 outputs, 27.9 GB.  Checked on whole slices
     (prefix digits fixed, the oracle's 16-D recurrence on the matching
-    sub-cubes), on random single outputs (the definition), and on the sum
-    invariant over all outputs."""
+    sub-cube pairs, summed over the pairs of the digit-1 axes), on random
+    single outputs (the definition), and on the sum invariant over all
+    outputs."""
     D = 20
     x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2020)
     xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
@@ -182,12 +183,23 @@ def test_d20_int64_full_size(hc):
     torch.cuda.synchronize()
     # sum invariant (no overflow: |sum z| <= (2^20 * 1000)^2)
     assert int(z.sum().item()) == int(x.sum()) * int(y.sum())
-    # slices with 4 leading digits fixed: digit 0 -> (0, 0), 2 -> (1, 1)
+    # slices with 4 leading digits fixed, by the direct form on those axes:
+    # digit 0 -> sub-cube pair (0, 0), 2 -> (1, 1), 1 -> (0, 1) + (1, 0); the
+    # slice is the sum over the pairs of the oracle's 16-D recurrence
     n16 = 3 ** 16
-    for digits in [(0, 0, 0, 0), (2, 2, 2, 2), (0, 2, 2, 0)]:
+    for digits in [(0, 0, 0, 0), (2, 2, 2, 2), (0, 2, 2, 0), (1, 0, 2, 1)]:
         off_z = sum(d * 3 ** (3 - i) for i, d in enumerate(digits)) * n16
-        sel = sum((d // 2) << (3 - i) for i, d in enumerate(digits)) << 16
-        want = oracle.convolve(x[sel:sel + (1 << 16)], y[sel:sel + (1 << 16)], threads=16)
+        want = np.zeros(n16, np.int64)
+        ones = [i for i, d in enumerate(digits) if d == 1]
+        for choice in range(1 << len(ones)):
+            bx = [d // 2 for d in digits]
+            for q, i in enumerate(ones):
+                bx[i] = (choice >> q) & 1
+            by = [d - b for d, b in zip(digits, bx)]
+            sx = sum(b << (3 - i) for i, b in enumerate(bx)) << 16
+            sy = sum(b << (3 - i) for i, b in enumerate(by)) << 16
+            with np.errstate(over="ignore"):
+                want += oracle.convolve(x[sx:sx + (1 << 16)], y[sy:sy + (1 << 16)], threads=16)
         got = z[off_z:off_z + n16].cpu().numpy()
         assert np.array_equal(got, want), digits
     g = np.random.default_rng(0)
