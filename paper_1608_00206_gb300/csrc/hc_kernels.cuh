@@ -90,10 +90,16 @@ inline cudaError_t launch_eval(int K, const typename M::In* sx, const typename M
 // Whether the pass double-buffers its tiles: only when two buffers still let
 // two CTAs share an SM (otherwise the lost occupancy costs more than the
 // overlap gains; measured on GB300).
+// Otherwise, when the next tile's round-1 pencil fits in registers beside
+// the current round-2 pencil (estimated 2 pencils + 24 registers a thread,
+// one CTA per SM), it is prefetched into registers (interp_tiles_regpipe).
 template <class M, int K1, int K2, int L>
 struct InterpPipe {
   static constexpr size_t kBuf = sizeof(typename M::W) * (size_t)p3(K1 + K2) * L;
   static constexpr bool kOn = K1 > 0 && 2 * kBuf <= 113 * 1024;
+  static constexpr int kThreads = (p3(K2) * L + 31) / 32 * 32;
+  static constexpr int kRegs = 2 * p3(K2) * (int)(sizeof(typename M::W) / 4) + 24;
+  static constexpr bool kReg = K1 > 0 && !kOn && kThreads * kRegs <= 65536;
   static constexpr size_t kSmem = K1 == 0 ? 0 : (kOn ? 2 * kBuf : kBuf);
 };
 
@@ -114,6 +120,16 @@ __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256) in
       base = h * p3(K1 + K2) * lo + l0;
     };
     interp_tiles_pipelined<M, K1, K2, L, FINAL, decltype(tile), TR>(src, dst_, lo, n, tile, smem);
+  } else if constexpr (InterpPipe<M, K1, K2, L>::kReg) {
+    const long long first = blockIdx.x, step = gridDim.x;
+    const int n = first < ntiles ? (int)((ntiles - 1 - first) / step + 1) : 0;
+    auto tile = [&](int i, long long& base, long long& l0) {
+      const long long t = first + (long long)i * step;
+      const long long h = t / ctiles;
+      l0 = (t - h * ctiles) * L;
+      base = h * p3(K1 + K2) * lo + l0;
+    };
+    interp_tiles_regpipe<M, K1, K2, L, FINAL, decltype(tile), TR>(src, dst_, lo, n, tile, smem);
   } else {
 #pragma unroll 1
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {

@@ -500,4 +500,79 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src,
   }
 }
 
+// Interpolation of k = K1 + K2 axes (K1 > 0) over a sequence of column
+// tiles with a register prefetch: each thread owns one round-1 pencil per
+// tile and loads the next tile's pencil into registers right after the
+// barrier that ends round 1, so those loads are in flight while round 2 of
+// the current tile runs (one smem buffer of 3^k * L elements; the register
+// copy doubles the bytes in flight without a second buffer).  Same
+// arithmetic and per-element order as interp_tile_body; src may equal dst
+// (tiles are disjoint, and a tile's elements are loaded before any of them
+// is stored).  Needs blockDim.x >= 3^max(K1,K2) * L.
+template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false>
+__device__ __forceinline__ void interp_tiles_regpipe(const typename M::W* src, void* dst_,
+                                                     long long lo, int n, const TileFn& tile,
+                                                     unsigned char* smem) {
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  constexpr int P1 = TR ? p3(K1) : p3(K2);        // round-1 pencil length
+  constexpr int N1 = (TR ? p3(K2) : p3(K1)) * L;  // round-1 pencils
+  constexpr int P2 = TR ? p3(K2) : p3(K1);        // round-2 pencil length
+  constexpr int N2 = (TR ? p3(K1) : p3(K2)) * L;  // round-2 pencils
+  W* T = reinterpret_cast<W*>(smem);
+  const int tid = threadIdx.x;
+  // round-1 pencil of this thread: a1 = outer index o (I) or inner index r (I^T)
+  const int a1 = tid / L, l1 = tid - a1 * L;
+  const int a2 = tid / L, l2 = tid - a2 * L;
+  auto row1 = [&](int j) { return TR ? j * p3(K2) + a1 : a1 * p3(K2) + j; };
+  auto row2 = [&](int j) { return TR ? a2 * p3(K2) + j : j * p3(K2) + a2; };
+  W pre[P1];
+  auto fetch = [&](int i) {
+    long long base, l0;
+    tile(i, base, l0);
+    if (tid < N1 && l0 + l1 < lo) {
+#pragma unroll
+      for (int j = 0; j < P1; ++j) pre[j] = src[base + (long long)row1(j) * lo + l1];
+    }
+  };
+  if (n > 0) fetch(0);
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    long long base, l0;
+    tile(i, base, l0);
+    if (tid < N1 && l0 + l1 < lo) {
+      W v[P1];
+#pragma unroll
+      for (int j = 0; j < P1; ++j) v[j] = pre[j];
+      if constexpr (TR)
+        interp_t_pencil<M, K1>(v);
+      else
+        interp_pencil<M, K2>(v);
+#pragma unroll
+      for (int j = 0; j < P1; ++j) T[row1(j) * L + l1] = v[j];
+    }
+    __syncthreads();
+    if (i + 1 < n) fetch(i + 1);
+    if (tid < N2 && l0 + l2 < lo) {
+      W v[P2];
+#pragma unroll
+      for (int j = 0; j < P2; ++j) v[j] = T[row2(j) * L + l2];
+      if constexpr (TR)
+        interp_t_pencil<M, K2>(v);
+      else
+        interp_pencil<M, K1>(v);
+      if constexpr (FINAL && !TR) {
+        Out* d = reinterpret_cast<Out*>(dst_);
+#pragma unroll
+        for (int j = 0; j < P2; ++j) d[base + (long long)row2(j) * lo + l2] = M::out(v[j]);
+      } else {
+        W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+        for (int j = 0; j < P2; ++j) d[base + (long long)row2(j) * lo + l2] = v[j];
+      }
+    }
+    __syncthreads();  // T is rewritten by the next tile's round 1
+  }
+}
+
 }  // namespace hc
