@@ -225,6 +225,21 @@ hc_status hc_convolve_backward(const void* dz, const void* x, const void* y, voi
  * in a CUDA graph and replayed; every replay recomputes the prepared batch.
  * Device-side waits are bounded: a wait that gives up records HC_ERR_TIMEOUT
  * in the workspace status word (read it with hc_device_status).
+ *
+ * Fusion depth.  An instance with D <= fused_max_d runs fused: all such
+ * instances share one persistent launch, each convolved in one piece (tiles,
+ * then its outer axes interpolated while it is in L2).  The others run
+ * grouped: per D, whole passes over all instances of that D (evaluation of
+ * the outer axes, one tile launch, one interpolation pass), a few launches
+ * per distinct D.  Both give the same bits.  hc_batched_prepare uses the
+ * built-in depth; hc_batched_prepare_split takes it explicitly (-1: every
+ * instance grouped except D = 0; >= 14, or 15 for HC_FP32: every instance
+ * fused; HC_ERR_ARG below -1); hc_batched_autotune times every depth that
+ * splits the batch differently, `reps` launches each after a warm-up, on
+ * `stream` with CUDA events (synchronising; the outputs are overwritten),
+ * returns the fastest in *best_fused_max_d (and its time in *best_ms unless
+ * NULL) and leaves the workspace prepared with it.
+ * hc_batched_workspace_size covers every depth.
  */
 typedef struct {
   const void* x;
@@ -243,6 +258,13 @@ hc_status hc_batched_prepare(const hc_instance* inst, int n, hc_dtype dtype, voi
 
 hc_status hc_batched_launch(void* workspace, size_t ws_bytes, hc_stream_t stream);
 
+hc_status hc_batched_prepare_split(const hc_instance* inst, int n, hc_dtype dtype, int fused_max_d,
+                                   void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+hc_status hc_batched_autotune(const hc_instance* inst, int n, hc_dtype dtype, void* workspace,
+                              size_t ws_bytes, int reps, hc_stream_t stream,
+                              int* best_fused_max_d, double* best_ms);
+
 /* Testing aid for the bounded waits (failure detection without a GPU fault):
  * rewrites the prepared work list in `workspace` so that the interpolation
  * tickets of `instance` wait for one more finished tile than the instance
@@ -251,7 +273,8 @@ hc_status hc_batched_launch(void* workspace, size_t ws_bytes, hc_stream_t stream
  * incomplete) and finishes every other instance.  hc_batched_prepare undoes
  * it.  Synchronous.  HC_ERR_ARG if the workspace was not prepared or the
  * instance is out of range.  Instances with D <= the tile axes (8; 9 for
- * HC_FP32) have no waits, so the call has no effect on them. */
+ * HC_FP32) and instances run grouped have no waits, so the call has no
+ * effect on them. */
 hc_status hc_batched_inject_stall(void* workspace, int instance);
 
 /* ------------------------------------------------------------------------

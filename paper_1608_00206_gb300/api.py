@@ -202,12 +202,16 @@ class BatchedConv:
 
     ``xs``, ``ys``: sequences of CUDA tensors (2^D_i elements each, one dtype,
     D_i <= 14, or 15 for float32).  The work list is built once
-    (hc_batched_prepare); :meth:`launch` runs the whole batch as one
-    persistent kernel and can be captured in a CUDA graph (:meth:`capture`),
-    whose replays recompute the batch from the current contents of xs, ys.
+    (hc_batched_prepare); :meth:`launch` runs the whole batch -- instances
+    with D <= ``fused_max_d`` in one persistent kernel, the others as
+    per-D grouped passes -- and can be captured in a CUDA graph
+    (:meth:`capture`), whose replays recompute the batch from the current
+    contents of xs, ys.  ``fused_max_d``: None = the library's default,
+    "tune" = the batched autotuner's choice (:attr:`fused_max_d` holds it).
     """
 
-    def __init__(self, xs, ys, outs=None, *, mixed: bool = False, stream=None):
+    def __init__(self, xs, ys, outs=None, *, mixed: bool = False, stream=None,
+                 fused_max_d=None):
         if len(xs) != len(ys):
             raise ValueError("xs and ys differ in length")
         self.n = len(xs)
@@ -237,9 +241,21 @@ class BatchedConv:
             raise ValueError("batch rejected (an instance has D out of range or bad buffers)")
         self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8,
                                      device=self.device)
-        check(lib.hc_batched_prepare(arr, self.n, self.code, self.workspace.data_ptr(),
-                                     self.ws_bytes, _stream(self.device, stream)),
-              "hc_batched_prepare")
+        st = _stream(self.device, stream)
+        self.fused_max_d = fused_max_d
+        if fused_max_d is None:
+            check(lib.hc_batched_prepare(arr, self.n, self.code, self.workspace.data_ptr(),
+                                         self.ws_bytes, st), "hc_batched_prepare")
+        elif fused_max_d == "tune":
+            best, ms = ctypes.c_int(), ctypes.c_double()
+            check(lib.hc_batched_autotune(arr, self.n, self.code, self.workspace.data_ptr(),
+                                          self.ws_bytes, 3, st, ctypes.byref(best),
+                                          ctypes.byref(ms)), "hc_batched_autotune")
+            self.fused_max_d, self.tuned_ms = int(best.value), float(ms.value)
+        else:
+            check(lib.hc_batched_prepare_split(arr, self.n, self.code, int(fused_max_d),
+                                               self.workspace.data_ptr(), self.ws_bytes, st),
+                  "hc_batched_prepare_split")
         self.graph = None
 
     def launch(self, stream=None):
@@ -273,9 +289,9 @@ class BatchedConv:
               "hc_batched_inject_stall")
 
 
-def convolve_batched(xs, ys, outs=None, *, mixed: bool = False, stream=None):
-    """One persistent launch over all instances; returns the list of outputs."""
-    b = BatchedConv(xs, ys, outs, mixed=mixed, stream=stream)
+def convolve_batched(xs, ys, outs=None, *, mixed: bool = False, stream=None, fused_max_d=None):
+    """All instances in one batched launch sequence; returns the list of outputs."""
+    b = BatchedConv(xs, ys, outs, mixed=mixed, stream=stream, fused_max_d=fused_max_d)
     return b.launch(stream)
 
 

@@ -30,20 +30,6 @@ namespace hc {
 
 // ---------------------------------------------------------------------------
 // K2 kernel: one tile per outer index alpha (grid-stride over tiles).
-template <class In>
-struct RowLoader {
-  const In* x;
-  const In* y;
-  __device__ __forceinline__ In operator()(int op, int i) const { return op ? y[i] : x[i]; }
-};
-
-// The tile's input rows come from a double buffer that cp.async fills with
-// the next tile's rows while the current tile is being computed.
-template <class M, int C>
-struct TileRows {
-  static constexpr size_t kOff = (TileSmem<M, C>::bytes + 15) / 16 * 16;
-  static constexpr size_t bytes = kOff + 2 * 2 * sizeof(typename M::In) * (size_t)p2(C);
-};
 
 template <class M, int C, bool FINAL>
 __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __restrict__ X,

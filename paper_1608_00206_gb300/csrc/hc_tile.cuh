@@ -83,6 +83,23 @@ struct TileSmem {
   static constexpr size_t bytes = kAlias ? kW : kW + (TileShape<C>::G >= 2 ? 2 * kLast : 0);
 };
 
+// Loader of a tile whose two operand rows are plain arrays (global or shared).
+template <class In>
+struct RowLoader {
+  const In* x;
+  const In* y;
+  __device__ __forceinline__ In operator()(int op, int i) const { return op ? y[i] : x[i]; }
+};
+
+// Shared memory of a tile kernel whose input rows come from a double buffer
+// that cp.async fills with the next tile's rows while the current tile is
+// being computed: the tile's own smem, then [buffer][operand][2^C] rows.
+template <class M, int C>
+struct TileRows {
+  static constexpr size_t kOff = (TileSmem<M, C>::bytes + 15) / 16 * 16;
+  static constexpr size_t bytes = kOff + 2 * 2 * sizeof(typename M::In) * (size_t)p2(C);
+};
+
 // Loader: ld(op, i) returns element i of the tile's operand row (op 0 = x,
 // 1 = y), already evaluated on the outer axes.  out_tile: the tile's 3^C
 // outputs.  smem: TileSmem<M, C>::bytes of shared memory.

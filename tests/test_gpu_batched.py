@@ -1,8 +1,10 @@
-"""GPU parity of the batching form (one persistent launch over many
-convolutions of uneven D): every instance bitwise equal to the oracle's
-recurrence in the same precision, the full 4096-instance workload equal to a
-per-instance loop of the plain kernel, CUDA-graph replay, and the bounded
-device-side wait that reports HC_ERR_TIMEOUT instead of hanging."""
+"""GPU parity of the batching form (many convolutions of uneven D; fused
+instances in one persistent launch, the others as per-D grouped passes):
+every instance bitwise equal to the oracle's recurrence in the same
+precision at every fusion depth, the full 4096-instance workload equal to a
+per-instance loop of the plain kernel, the batched autotuner, CUDA-graph
+replay, and the bounded device-side wait that reports HC_ERR_TIMEOUT instead
+of hanging."""
 import numpy as np
 import pytest
 
@@ -31,8 +33,11 @@ def bits(a):
     return a.view(np.uint64) if a.dtype.itemsize == 8 else a.view(np.uint32)
 
 
+@pytest.mark.parametrize("split", [None, -1, 5, 15])
 @pytest.mark.parametrize("kind", ["int64", "float64", "float32", "mixed"])
-def test_batched_every_dim_bit_exact(hc, kind):
+def test_batched_every_dim_bit_exact(hc, kind, split):
+    """Every D from 0 to the limit, repeated D included, at the default fusion
+    depth, all grouped (-1), a split in the middle (5) and all fused (15)."""
     dims = list(range(0, 15)) + [14, 3, 9, 0, 12]
     if kind == "float32":
         dims.append(15)
@@ -45,7 +50,7 @@ def test_batched_every_dim_bit_exact(hc, kind):
         else:
             pairs.append(inputs.uniform01_pair(D, seed=i))
     outs = hc.convolve_batched([T(x) for x, _ in pairs], [T(y) for _, y in pairs],
-                               mixed=(kind == "mixed"))
+                               mixed=(kind == "mixed"), fused_max_d=split)
     torch.cuda.synchronize()
     for (x, y), z, D in zip(pairs, outs, dims):
         want = oracle.convolve_mixed(x, y) if kind == "mixed" else oracle.convolve(x, y, threads=8)
@@ -92,6 +97,21 @@ def test_batched_4096_float32_workload(hc):
     assert b.status() == 0
 
 
+def test_batched_autotune_picks_a_depth(hc):
+    """The batched autotuner tries every fusion depth that splits the batch,
+    leaves the winner prepared, and the result is bitwise the same."""
+    dims, pairs = _workload(n=256, seed=77)
+    xs = [T(x) for x, _ in pairs]
+    ys = [T(y) for _, y in pairs]
+    b = hc.BatchedConv(xs, ys, fused_max_d="tune")
+    assert -1 <= b.fused_max_d <= 15 and b.tuned_ms > 0
+    outs = [o.clone() for o in b.launch()]
+    ref = hc.BatchedConv(xs, ys, fused_max_d=15)
+    for o, r in zip(outs, ref.launch()):
+        assert torch.equal(o.view(torch.int32), r.view(torch.int32))
+    assert b.status() == 0
+
+
 def test_bounded_wait_reports_timeout(hc):
     """A stall injected on the host (an instance's interpolation tickets wait
     for a tile that does not exist) ends in HC_ERR_TIMEOUT after about a
@@ -99,7 +119,8 @@ def test_bounded_wait_reports_timeout(hc):
     usable."""
     dims = [10, 11, 7, 12]
     pairs = [inputs.uniform_int_pair(D, -1000, 1000, seed=D) for D in dims]
-    b = hc.BatchedConv([T(x) for x, _ in pairs], [T(y) for _, y in pairs])
+    # all fused: only the persistent launch has waits
+    b = hc.BatchedConv([T(x) for x, _ in pairs], [T(y) for _, y in pairs], fused_max_d=15)
     b.inject_stall(1)
     b.launch()
     assert b.status() == _lib.HC_ERR_TIMEOUT
@@ -107,7 +128,7 @@ def test_bounded_wait_reports_timeout(hc):
         want = oracle.convolve(*pairs[i])
         assert np.array_equal(b.outs[i].cpu().numpy().reshape(-1), want)
     # the same workspace prepared again runs clean
-    b2 = hc.BatchedConv([T(x) for x, _ in pairs], [T(y) for _, y in pairs])
+    b2 = hc.BatchedConv([T(x) for x, _ in pairs], [T(y) for _, y in pairs], fused_max_d=15)
     b2.launch()
     assert b2.status() == 0
     assert np.array_equal(b2.outs[1].cpu().numpy().reshape(-1), oracle.convolve(*pairs[1]))
