@@ -123,18 +123,42 @@ __global__ void __launch_bounds__(256) group_tile_kernel(const GroupPtrs* __rest
 
 // Interpolation of the a = K1 + K2 outer axes of every instance of a group,
 // in place on its [3^a][lo] intermediate (FINAL: written to its output in
-// the output type).  Tile t: instance t / per, columns (t % per) * L ...
+// the output type).  Tile t: instance t / per, columns (t % per) * L ...;
+// the same three tile loops as interp_pass_kernel (double-buffered cp.async,
+// register prefetch, or one tile at a time), each tile on its instance's
+// arrays.
 template <class M, int K1, int K2, int L, bool FINAL>
 __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256)
     group_interp_kernel(const GroupPtrs* __restrict__ tab, long long lo, long long per,
                         long long ntiles) {
   typedef typename M::W W;
   extern __shared__ __align__(16) unsigned char smem[];
+  if constexpr (K1 > 0 && (InterpPipe<M, K1, K2, L>::kOn || InterpPipe<M, K1, K2, L>::kReg)) {
+    const long long first = blockIdx.x, step = gridDim.x;
+    const int n = first < ntiles ? (int)((ntiles - 1 - first) / step + 1) : 0;
+    auto tile = [&](int i, long long& base, long long& l0) {
+      const long long t = first + (long long)i * step;
+      l0 = (t - t / per * per) * L;
+      base = l0;
+    };
+    auto ptrs = [&](int i, const W*& s, void*& d) {
+      const long long inst = (first + (long long)i * step) / per;
+      s = reinterpret_cast<const W*>(tab[inst].w);
+      d = FINAL ? tab[inst].z : tab[inst].w;
+    };
+    if constexpr (InterpPipe<M, K1, K2, L>::kOn)
+      interp_tiles_pipelined<M, K1, K2, L, FINAL, decltype(tile), false, decltype(ptrs)>(
+          nullptr, nullptr, lo, n, tile, smem, ptrs);
+    else
+      interp_tiles_regpipe<M, K1, K2, L, FINAL, decltype(tile), false, decltype(ptrs)>(
+          nullptr, nullptr, lo, n, tile, smem, ptrs);
+  } else {
 #pragma unroll 1
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long i = t / per, l0 = (t - i * per) * L;
-    interp_tile_body<M, K1, K2, L, FINAL, false>(reinterpret_cast<const W*>(tab[i].w),
-                                                 FINAL ? tab[i].z : tab[i].w, l0, l0, lo, smem);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const long long i = t / per, l0 = (t - i * per) * L;
+      interp_tile_body<M, K1, K2, L, FINAL, false>(reinterpret_cast<const W*>(tab[i].w),
+                                                   FINAL ? tab[i].z : tab[i].w, l0, l0, lo, smem);
+    }
   }
 }
 
@@ -374,8 +398,10 @@ static cudaError_t launch_group_tile(int C, const GroupPtrs* tab, const typename
 template <class M, int K1, int K2, bool FINAL>
 static cudaError_t launch_group_interp_k(const GroupPtrs* tab, int n, long long lo,
                                          cudaStream_t st) {
-  constexpr int L = K1 > 0 ? (sizeof(typename M::W) == 4 ? 32 : 16) : 256;
-  constexpr size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
+  // columns per tile: 32, except 16 for 8-byte intermediates below 6 axes
+  // (two 16-column buffers double-buffer at two CTAs per SM)
+  constexpr int L = K1 == 0 ? 256 : (sizeof(typename M::W) == 8 && K1 + K2 < 6 ? 16 : 32);
+  constexpr size_t smem = K1 > 0 ? InterpPipe<M, K1, K2, L>::kSmem : 0;
   constexpr int threads = K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256;
   auto k = group_interp_kernel<M, K1, K2, L, FINAL>;
   ProfileScope prof(st, "batched_interp");

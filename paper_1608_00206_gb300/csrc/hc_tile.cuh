@@ -2,6 +2,8 @@
 // persistent batched kernel.
 #pragma once
 
+#include <type_traits>
+
 #include "hc_common.cuh"
 
 namespace hc {
@@ -410,6 +412,11 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
   }
 }
 
+// Per-tile array pointers for the multi-tile interpolation loops: by default
+// every tile uses the loop's src / dst; a PtrFn `ptrs(i, src, dst)` gives
+// tile i its own arrays (the grouped batched form: one array per instance).
+struct NoPtrs {};
+
 // Pipelined interpolation of k = K1 + K2 axes (K1 > 0) over a sequence of
 // column tiles.  Tile i is rows base_i + j * lo (j < 3^k), columns
 // l0_i + [0, L) clipped to lo.  Its elements are copied into shared buffer
@@ -417,10 +424,12 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
 // interpolates the inner K2 axes in place in shared memory, round 2 the outer
 // K1 axes from shared memory to dst.  smem: 2 * 3^k * L W elements.
 // `tile(i, base, l0)` yields the position of tile i; n tiles in all.
-template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false>
-__device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src, void* dst_,
+template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false,
+          class PtrFn = NoPtrs>
+__device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src0, void* dst0,
                                                        long long lo, int n, const TileFn& tile,
-                                                       unsigned char* smem) {
+                                                       unsigned char* smem,
+                                                       const PtrFn& ptrs = PtrFn()) {
   typedef typename M::W W;
   typedef typename M::Out Out;
   constexpr int ROWS = p3(K1 + K2);
@@ -428,9 +437,20 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src,
   W* buf0 = reinterpret_cast<W*>(smem);
   W* buf1 = buf0 + NE;
   const int tid = threadIdx.x, nt = blockDim.x;
+  auto arrays = [&](int i, const W*& s, void*& d) {
+    if constexpr (std::is_same<PtrFn, NoPtrs>::value) {
+      s = src0;
+      d = dst0;
+    } else {
+      ptrs(i, s, d);
+    }
+  };
   auto prefetch = [&](int i, W* b) {
     long long base, l0;
     tile(i, base, l0);
+    const W* src;
+    void* dd;
+    arrays(i, src, dd);
 #pragma unroll 1
     for (int e = tid; e < NE; e += nt) {
       const int row = e / L, l = e - row * L;
@@ -451,6 +471,9 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src,
     __syncthreads();  // tile i's elements are in b
     long long base, l0;
     tile(i, base, l0);
+    const W* src_i;
+    void* dst_;
+    arrays(i, src_i, dst_);
     if constexpr (TR) {
       // I^T: round 1 the outer K1 axes in place, round 2 the inner K2 axes
 #pragma unroll 1
@@ -526,10 +549,12 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src,
 // arithmetic and per-element order as interp_tile_body; src may equal dst
 // (tiles are disjoint, and a tile's elements are loaded before any of them
 // is stored).  Needs blockDim.x >= 3^max(K1,K2) * L.
-template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false>
-__device__ __forceinline__ void interp_tiles_regpipe(const typename M::W* src, void* dst_,
+template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false,
+          class PtrFn = NoPtrs>
+__device__ __forceinline__ void interp_tiles_regpipe(const typename M::W* src0, void* dst0,
                                                      long long lo, int n, const TileFn& tile,
-                                                     unsigned char* smem) {
+                                                     unsigned char* smem,
+                                                     const PtrFn& ptrs = PtrFn()) {
   typedef typename M::W W;
   typedef typename M::Out Out;
   constexpr int P1 = TR ? p3(K1) : p3(K2);        // round-1 pencil length
@@ -543,10 +568,21 @@ __device__ __forceinline__ void interp_tiles_regpipe(const typename M::W* src, v
   const int a2 = tid / L, l2 = tid - a2 * L;
   auto row1 = [&](int j) { return TR ? j * p3(K2) + a1 : a1 * p3(K2) + j; };
   auto row2 = [&](int j) { return TR ? a2 * p3(K2) + j : j * p3(K2) + a2; };
+  auto arrays = [&](int i, const W*& s, void*& d) {
+    if constexpr (std::is_same<PtrFn, NoPtrs>::value) {
+      s = src0;
+      d = dst0;
+    } else {
+      ptrs(i, s, d);
+    }
+  };
   W pre[P1];
   auto fetch = [&](int i) {
     long long base, l0;
     tile(i, base, l0);
+    const W* src;
+    void* dd;
+    arrays(i, src, dd);
     if (tid < N1 && l0 + l1 < lo) {
 #pragma unroll
       for (int j = 0; j < P1; ++j) pre[j] = src[base + (long long)row1(j) * lo + l1];
@@ -557,6 +593,9 @@ __device__ __forceinline__ void interp_tiles_regpipe(const typename M::W* src, v
   for (int i = 0; i < n; ++i) {
     long long base, l0;
     tile(i, base, l0);
+    const W* src_i;
+    void* dst_;
+    arrays(i, src_i, dst_);
     if (tid < N1 && l0 + l1 < lo) {
       W v[P1];
 #pragma unroll
