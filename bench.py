@@ -292,6 +292,16 @@ class Workload:
                 return 3 ** ap * (3 ** m * tile + 2 * m * 3 ** (C + m - 1)), "alu"
             # read the operands evaluated on ev axes, write the 3^D intermediate once
             return 2 * 3 ** ev * 2 ** (D - ev) * s + 3 ** D * sw, "hbm"
+        if kname == "eval_pass" and self.name != "fwdbwd":
+            # whole-array evaluation passes of <= 3 axes over the ev outer
+            # axes: each reads and writes both operands
+            _, _, _, _, ev = self.schedule_geometry()
+            total, d0 = 0, 0
+            while d0 < ev:
+                k = min(3, ev - d0)
+                total += 2 * s * (3 ** d0 * 2 ** (D - d0) + 3 ** (d0 + k) * 2 ** (D - d0 - k))
+                d0 += k
+            return total / max(launches_per_step, 1), "hbm"
         if self.name == "d16_fp64":
             return self._fp64_ops(kname, launches_per_step), "alu"
         if kname in ("interp_pass", "interp_t_pass"):
