@@ -122,7 +122,9 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  *                      typically with hc_autotune's winner).
  * Fields: c in 0..9 for HC_FP32, 0..8 otherwise (0 = the largest; clamped to
  * D); k in 0..6 (0 = 6); cols = columns per whole-array interpolation tile,
- * 8, 16 or 32 (0 = 32 for 4-byte and 16 for 8-byte intermediates).
+ * 8, 16 or 32, each element copied on its own (0 = 32 for 4-byte and 16 for
+ * 8-byte intermediates), or -16 / -32: 16 or 32 columns whose rows are copied
+ * in 16-byte pieces (each row widened to 16-byte boundaries).
  * HC_ERR_ARG for fields out of range. */
 #define HC_SCHED_DEFAULT 0
 #define HC_SCHED_PASSES 1

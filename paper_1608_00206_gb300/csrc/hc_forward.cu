@@ -345,7 +345,8 @@ bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
   const int cmax = dtype == HC_FP32 ? 9 : 8;
   if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_CHUNKED) return false;
   if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
-  return s.cols == 0 || s.cols == 8 || s.cols == 16 || s.cols == 32;
+  return s.cols == 0 || s.cols == 8 || s.cols == 16 || s.cols == 32 || s.cols == -16 ||
+         s.cols == -32;
 }
 
 hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
@@ -414,10 +415,10 @@ static std::vector<hc_schedule> tune_candidates(int D, hc_dtype dtype) {
     v.push_back({HC_SCHED_CHUNKED, 0, 0, 0});
     return v;
   }
-  const int cols[3] = {8, 16, 32};
+  const int cols[5] = {8, 16, 32, -16, -32};
   for (int c = cmax - 1; c <= cmax; ++c) {
     for (int k = 3; k <= 6; ++k)
-      for (int ci = 0; ci < 3; ++ci) {
+      for (int ci = 0; ci < 5; ++ci) {
         v.push_back({HC_SCHED_PASSES, c, k, cols[ci]});
         v.push_back({HC_SCHED_CHUNKED, c, k, cols[ci]});
       }

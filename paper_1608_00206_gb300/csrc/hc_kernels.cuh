@@ -141,6 +141,25 @@ __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256) in
   }
 }
 
+// K3 with 16-byte row copies (interp_tiles_wide).
+template <class M, int K1, int K2, int L, bool FINAL, bool TR>
+__global__ void __launch_bounds__((p3(K2) * L + 31) / 32 * 32) interp_wide_kernel(const typename M::W* src, void* dst_,
+                                                          long long hi, long long lo) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const long long ctiles = (lo + L - 1) / L;
+  const long long ntiles = hi * ctiles;
+  const long long first = blockIdx.x, step = gridDim.x;
+  const int n = first < ntiles ? (int)((ntiles - 1 - first) / step + 1) : 0;
+  auto tile = [&](int i, long long& base, long long& l0) {
+    const long long t = first + (long long)i * step;
+    const long long h = t / ctiles;
+    l0 = (t - h * ctiles) * L;
+    base = h * p3(K1 + K2) * lo + l0;
+  };
+  interp_tiles_wide<M, K1, K2, L, FINAL, decltype(tile), TR>(src, dst_, lo, hi * p3(K1 + K2) * lo, n,
+                                                             tile, smem);
+}
+
 // Columns per whole-array interpolation tile (the schedule's `cols`).
 template <class M>
 inline int default_cols() {
@@ -166,6 +185,23 @@ inline cudaError_t launch_interp_kl(const typename M::W* src, void* dst, long lo
   return cudaGetLastError();
 }
 
+// The same pass with 16-byte row copies (interp_wide_kernel).
+template <class M, int K1, int K2, int L, bool FINAL, bool TR>
+inline cudaError_t launch_wide_kl(const typename M::W* src, void* dst, long long hi, long long lo,
+                                  cudaStream_t st) {
+  typedef WideRows<M, K1, K2, L> WR;
+  auto k = interp_wide_kernel<M, K1, K2, L, FINAL, TR>;
+  ProfileScope prof(st, TR ? "interp_t_pass" : "interp_pass");
+  cudaError_t e = prep_kernel(k, WR::kSmem);
+  if (e != cudaSuccess) return e;
+  const int threads = (p3(K2) * L + 31) / 32 * 32;
+  const long long ntiles = hi * ((lo + L - 1) / L);
+  k<<<grid_for(k, threads, WR::kSmem, ntiles), threads, WR::kSmem, st>>>(src, dst, hi, lo);
+  return cudaGetLastError();
+}
+
+// cols: 8, 16, 32 columns per tile with per-element copies; -16, -32: 16 or
+// 32 columns with 16-byte row copies.
 template <class M, int K1, int K2, bool FINAL, bool TR>
 inline cudaError_t launch_interp_k(int cols, const typename M::W* src, void* dst, long long hi,
                                    long long lo, cudaStream_t st) {
@@ -174,6 +210,8 @@ inline cudaError_t launch_interp_k(int cols, const typename M::W* src, void* dst
     case 8: return launch_interp_kl<M, K1, K2, 8, FINAL, TR>(src, dst, hi, lo, st);
     case 16: return launch_interp_kl<M, K1, K2, 16, FINAL, TR>(src, dst, hi, lo, st);
     case 32: return launch_interp_kl<M, K1, K2, 32, FINAL, TR>(src, dst, hi, lo, st);
+    case -16: return launch_wide_kl<M, K1, K2, 16, FINAL, TR>(src, dst, hi, lo, st);
+    case -32: return launch_wide_kl<M, K1, K2, 32, FINAL, TR>(src, dst, hi, lo, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -183,7 +221,7 @@ inline cudaError_t launch_interp_k(int cols, const typename M::W* src, void* dst
 template <class M, bool FINAL, bool TR = false>
 inline cudaError_t launch_interp(int k, int cols, const typename M::W* src, void* dst,
                                  long long hi, long long lo, cudaStream_t st) {
-  if (cols <= 0) cols = default_cols<M>();
+  if (cols == 0) cols = default_cols<M>();
   switch (k) {
     case 1: return launch_interp_k<M, 0, 1, FINAL, TR>(cols, src, dst, hi, lo, st);
     case 2: return launch_interp_k<M, 0, 2, FINAL, TR>(cols, src, dst, hi, lo, st);

@@ -631,4 +631,167 @@ __device__ __forceinline__ void interp_tiles_regpipe(const typename M::W* src0, 
   }
 }
 
+// 16-byte asynchronous copy global -> shared of `bytes` (<= 16) bytes, the
+// rest of the 16 zero-filled.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+
+// Tiles of k = K1 + K2 rows loaded with 16-byte copies: a row segment of L
+// columns starts at element base + j * lo, which for an odd lo is generally
+// not 16-byte aligned, so each row is widened to the enclosing aligned range
+// (row stride RS = L + A - 1 rounded up to A = 16 / s elements) and indexed
+// from its own offset (base + j * lo) mod A.  One copy instruction moves A
+// elements: a quarter (4-byte) or half (8-byte) of the load instructions of
+// the per-element copies, which bound the other loops.
+template <class M, int K1, int K2, int L>
+struct WideRows {
+  typedef typename M::W W;
+  static constexpr int A = 16 / (int)sizeof(W);
+  static constexpr int RS = (L + A - 1 + A - 1) / A * A;
+  static constexpr int NC = RS / A;  // 16-byte chunks per row
+  static constexpr int ROWS = p3(K1 + K2);
+  static constexpr size_t kBuf = sizeof(W) * (size_t)ROWS * RS;
+  // two buffers when they fit in a CTA's shared memory
+  static constexpr int NB = 2 * kBuf <= 220 * 1024 ? 2 : 1;
+  static constexpr size_t kSmem = NB * kBuf;
+};
+
+// Same arithmetic and per-element order as interp_tile_body; src may equal
+// dst.  N: elements of every source array (copies stop at its end).  NB = 2:
+// tile i + 1 is copied while tile i is interpolated.
+template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false,
+          class PtrFn = NoPtrs>
+__device__ __forceinline__ void interp_tiles_wide(const typename M::W* src0, void* dst0,
+                                                  long long lo, long long N, int n,
+                                                  const TileFn& tile, unsigned char* smem,
+                                                  const PtrFn& ptrs = PtrFn()) {
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  typedef WideRows<M, K1, K2, L> S;
+  constexpr int A = S::A, RS = S::RS, NC = S::NC, ROWS = S::ROWS, NB = S::NB;
+  constexpr int NE = ROWS * RS;
+  W* buf0 = reinterpret_cast<W*>(smem);
+  W* buf1 = buf0 + (NB == 2 ? NE : 0);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto arrays = [&](int i, const W*& s, void*& d) {
+    if constexpr (std::is_same<PtrFn, NoPtrs>::value) {
+      s = src0;
+      d = dst0;
+    } else {
+      ptrs(i, s, d);
+    }
+  };
+  auto fill = [&](int i, W* b) {
+    long long base, l0;
+    tile(i, base, l0);
+    const W* src;
+    void* dd;
+    arrays(i, src, dd);
+#pragma unroll 1
+    for (int e = tid; e < ROWS * NC; e += nt) {
+      const int row = e / NC, q = e - row * NC;
+      const long long c = ((base + (long long)row * lo) & ~(long long)(A - 1)) + (long long)q * A;
+      if (c < N) {
+        const long long left = N - c;
+        cp_async16(b + row * RS + q * A, src + c,
+                   (int)(left < A ? left * (long long)sizeof(W) : 16));
+      }
+    }
+    cp_async_commit();
+  };
+  if constexpr (NB == 2) {
+    if (n > 0) fill(0, buf0);
+  }
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    W* b = (NB == 2 && (i & 1)) ? buf1 : buf0;
+    if constexpr (NB == 2) {
+      if (i + 1 < n) {
+        fill(i + 1, (i & 1) ? buf0 : buf1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {
+      fill(i, b);
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // tile i's rows are in b
+    long long base, l0;
+    tile(i, base, l0);
+    const W* src_i;
+    void* dst_;
+    arrays(i, src_i, dst_);
+    const int bm = (int)(base & (A - 1)), lm = (int)(lo & (A - 1));
+    auto at = [&](int row, int col) -> W& {
+      return b[row * RS + ((bm + row * lm) & (A - 1)) + col];
+    };
+    if constexpr (TR) {
+      // I^T: round 1 the outer K1 axes in place, round 2 the inner K2 axes
+#pragma unroll 1
+      for (int p = tid; p < p3(K2) * L; p += nt) {
+        const int r = p / L, l = p - r * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K1)];
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) v[j] = at(j * p3(K2) + r, l);
+        interp_t_pencil<M, K1>(v);
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) at(j * p3(K2) + r, l) = v[j];
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int p = tid; p < p3(K1) * L; p += nt) {
+        const int o = p / L, l = p - o * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = at(o * p3(K2) + j, l);
+        interp_t_pencil<M, K2>(v);
+        W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) d[base + (long long)(o * p3(K2) + j) * lo + l] = v[j];
+      }
+    } else {
+      // round 1: inner K2 axes, in place
+#pragma unroll 1
+      for (int p = tid; p < p3(K1) * L; p += nt) {
+        const int o = p / L, l = p - o * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = at(o * p3(K2) + j, l);
+        interp_pencil<M, K2>(v);
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) at(o * p3(K2) + j, l) = v[j];
+      }
+      __syncthreads();
+      // round 2: outer K1 axes, shared -> global
+#pragma unroll 1
+      for (int p = tid; p < p3(K2) * L; p += nt) {
+        const int r = p / L, l = p - r * L;
+        if (l0 + l >= lo) continue;
+        W v[p3(K1)];
+#pragma unroll
+        for (int j = 0; j < p3(K1); ++j) v[j] = at(j * p3(K2) + r, l);
+        interp_pencil<M, K1>(v);
+        if constexpr (FINAL) {
+          Out* d = reinterpret_cast<Out*>(dst_);
+#pragma unroll
+          for (int j = 0; j < p3(K1); ++j)
+            d[base + (long long)(j * p3(K2) + r) * lo + l] = M::out(v[j]);
+        } else {
+          W* d = reinterpret_cast<W*>(dst_);
+#pragma unroll
+          for (int j = 0; j < p3(K1); ++j) d[base + (long long)(j * p3(K2) + r) * lo + l] = v[j];
+        }
+      }
+    }
+    __syncthreads();  // b is refilled by a later tile
+  }
+}
+
 }  // namespace hc

@@ -15,8 +15,24 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def L():
+    """The library with the built-in default schedules for the duration of
+    the module (a tuned table installed by an earlier test in the same
+    process is put back afterwards)."""
     build()
-    return _lib.lib()
+    lib = _lib.lib()
+    saved = {}
+    for D in range(_lib.HC_MAX_D + 1):
+        for dt in range(4):
+            s = _lib.hc_schedule()
+            assert lib.hc_get_default_schedule(D, dt, ctypes.byref(s)) == 0
+            saved[D, dt] = s
+            assert lib.hc_set_default_schedule(D, dt, None) == 0
+    yield lib
+    for (D, dt), s in saved.items():
+        builtin = _lib.hc_schedule()
+        lib.hc_get_default_schedule(D, dt, ctypes.byref(builtin))
+        if s.as_dict() != builtin.as_dict():
+            assert lib.hc_set_default_schedule(D, dt, ctypes.byref(s)) == 0
 
 
 def _declared():
@@ -106,11 +122,17 @@ def test_argument_errors_caught_on_host(L):
     # workspace overlapping the output
     assert conv(x, y, zz, 20, _lib.HC_INT64, zz, big, None) == _lib.HC_ERR_ALIAS
     # explicit schedules out of range
-    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (3, 0, 0, 0), (1, 0, 0, 12), (-1, 0, 0, 0)]:
+    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (3, 0, 0, 0), (1, 0, 0, 12), (-1, 0, 0, 0),
+                (1, 0, 0, -8), (2, 0, 0, -64)]:
         s = _lib.hc_schedule(*bad)
         assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, ctypes.byref(s), ws, size,
                                       None) == _lib.HC_ERR_ARG
         assert L.hc_set_default_schedule(10, _lib.HC_INT64, ctypes.byref(s)) == _lib.HC_ERR_ARG
+    # 16-byte row copies are a valid tile width
+    for good in [(1, 8, 6, -16), (2, 8, 6, -32)]:
+        s = _lib.hc_schedule(*good)
+        assert L.hc_set_default_schedule(10, _lib.HC_INT64, ctypes.byref(s)) == _lib.HC_OK
+    assert L.hc_set_default_schedule(10, _lib.HC_INT64, None) == _lib.HC_OK
     assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, None, ws, size, None) == \
         _lib.HC_ERR_ARG
     assert L.hc_device_status(None, None) == _lib.HC_ERR_ARG

@@ -129,6 +129,36 @@ def test_mixed_chunked_schedules(hc, c, m):
     assert_bit_equal(gpu_conv(hc, x, y, mixed=True, c=c, m=m), oracle.convolve_mixed(x, y))
 
 
+@pytest.mark.parametrize("cols", [8, 16, 32, -16, -32])
+@pytest.mark.parametrize("kind", ["int64", "float64", "float32", "mixed"])
+def test_every_interpolation_tile_width(hc, kind, cols):
+    """Whole-array interpolation passes of 4, 5 and 6 axes at every tile
+    width, with per-element copies (cols > 0) and with 16-byte row copies of
+    widened rows (cols < 0); lo = 3^c gives ragged column tiles and rows at
+    every 16-byte offset."""
+    D = 12
+    if kind == "int64":
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=abs(cols))
+        want = oracle.convolve(x, y)
+    elif kind == "mixed":
+        x, y = inputs.uniform01_pair(D, seed=abs(cols))
+        want = oracle.convolve_mixed(x, y)
+    else:
+        x, y = inputs.normal_pair(D, seed=abs(cols), dtype=np.float64 if kind == "float64" else np.float32)
+        want = oracle.convolve(x, y, threads=8)
+    for c, kmax in [(6, 6), (7, 5), (8, 4)]:
+        assert_bit_equal(gpu_conv(hc, x, y, mixed=(kind == "mixed"), c=c, kmax=kmax, cols=cols), want)
+
+
+@pytest.mark.parametrize("cols", [-16, -32, 8])
+def test_chunked_outer_passes_tile_width(hc, cols):
+    """The chunked schedule's whole-array passes (7 outer axes: 4 + 3) at a
+    forced tile width."""
+    D = 15
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=15)
+    assert_bit_equal(gpu_conv(hc, x, y, c=4, m=4, cols=cols), oracle.convolve(x, y, threads=16))
+
+
 def test_mixed_every_schedule(hc):
     D = 12
     x, y = inputs.uniform01_pair(D, seed=5)
