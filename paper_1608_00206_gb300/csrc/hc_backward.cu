@@ -20,6 +20,7 @@
 
 #include "hc_common.cuh"
 #include "hc_profile.cuh"
+#include "hc_forward.cuh"
 #include "hc_kernels.cuh"
 
 namespace hc {
@@ -482,14 +483,17 @@ static cudaError_t run_backward(const BwdPlan& p, const void* dz, const void* x,
     return cudaGetLastError();
   }
   cudaError_t e;
-  // I^T on the outer axes: dz -> G (the first pass copies out of dz)
+  // I^T on the outer axes: dz -> G (the first pass copies out of dz).  The
+  // passes have the shape of the forward's whole-array passes for the same
+  // (D, dtype), so they take the tile width of its default schedule.
+  const int cols = resolve_schedule(D, p.dtype, nullptr).cols;
   const W* G = (const W*)dz;
   W* Gbuf = (W*)(ws + p.off_g);
   for (int i = 0; i < p.n_it; ++i) {
     const int d0 = p.it_d0[i], k = p.it_k[i];
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
-    e = launch_interp<M, false, true>(k, 0, G, Gbuf, hi, lo, st);
+    e = launch_interp<M, false, true>(k, cols, G, Gbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
     G = Gbuf;
   }

@@ -55,6 +55,39 @@ def test_fp_adjoint_bit_exact(hc, dt, D):
     assert np.array_equal(bits(dx), bits(wx)) and np.array_equal(bits(dy), bits(wy))
 
 
+@pytest.mark.parametrize("cols", [8, 16, 32, -16, -32])
+@pytest.mark.parametrize("dt", [np.int64, np.float64, np.float32])
+def test_adjoint_every_tile_width(hc, dt, cols):
+    """The adjoint's I^T passes take the tile width of the forward default
+    schedule for (D, dtype): installed here through the library's default
+    table, every width (per-element and 16-byte row copies) gives the
+    oracle's bits.  D = 14: six outer axes in one transposed pass, ragged
+    column tiles, rows at every 16-byte offset."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib
+    D = 14
+    code = {np.int64: _lib.HC_INT64, np.float64: _lib.HC_FP64, np.float32: _lib.HC_FP32}[dt]
+    if dt == np.int64:
+        x, y = inputs.uniform_int_pair(D, -100, 100, seed=7)
+        dz = np.random.default_rng(7).integers(-100, 101, size=3 ** D, dtype=np.int64)
+    else:
+        x, y = inputs.normal_pair(D, seed=7, dtype=dt)
+        dz = inputs.normal(3 ** D, seed=8, dtype=dt)
+    hc.convolve(T(x), T(y))  # installs the shipped table, as any first call does
+    lib = _lib.lib()
+    saved = _lib.hc_schedule()
+    assert lib.hc_get_default_schedule(D, code, ctypes.byref(saved)) == 0
+    s = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 6, cols)
+    assert lib.hc_set_default_schedule(D, code, ctypes.byref(s)) == 0
+    try:
+        dx, dy = gpu_adj(hc, dz, x, y)
+    finally:
+        assert lib.hc_set_default_schedule(D, code, ctypes.byref(saved)) == 0
+    wx, wy = oracle.adjoint(dz, x, y)
+    assert np.array_equal(bits(dx), bits(wx)) and np.array_equal(bits(dy), bits(wy))
+
+
 def test_one_sided(hc):
     D = 11
     x, y = inputs.normal_pair(D, seed=1, dtype=np.float64)
