@@ -163,6 +163,24 @@ hc_status hc_autotune(const void* x, const void* y, void* z, int D, hc_dtype dty
                       hc_schedule* best, double* best_ms);
 
 /* ------------------------------------------------------------------------
+ * Separate output.  hc_convolve interpolates in place in z, so every pass
+ * reads and writes it.  hc_convolve_out keeps that 3^D intermediate in `w`
+ * (device memory, 3^D elements of the dtype, 16-byte aligned, overlapping
+ * nothing else; NULL and unused for HC_FP32_MIXED, whose intermediate is in
+ * the workspace) and writes z once, with the final stores: z may then be
+ * any memory the device can store to, e.g. page-locked host memory, so the
+ * result leaves the GPU while it is being computed, without a separate
+ * copy.  Same schedule, workspace and bits as hc_convolve.  HC_ERR_ARG if w
+ * is NULL for an exact or float dtype, or given for HC_FP32_MIXED;
+ * HC_ERR_ALIAS if w overlaps x, y, z or the workspace; HC_ERR_ARG, before
+ * anything is launched, if z is not device, managed or page-locked host
+ * memory mapped at its own address, or w is not device or managed memory
+ * (checked with cudaPointerGetAttributes, so the pointers must be known to
+ * the CUDA runtime). */
+hc_status hc_convolve_out(const void* x, const void* y, void* w, void* z, int D, hc_dtype dtype,
+                          void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * No-allocation form.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory at the call site -- code
  * running while another framework owns the device's memory pool,

@@ -54,6 +54,7 @@ SIGNATURES = {
     "hc_batched_prepare": (_i, [ctypes.POINTER(hc_instance), _i, _i, _vp, _sz, _vp]),
     "hc_batched_launch": (_i, [_vp, _sz, _vp]),
     "hc_batched_inject_stall": (_i, [_vp, _i]),
+    "hc_convolve_out": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _sz, _vp]),
     "hc_batched_prepare_split": (_i, [ctypes.POINTER(hc_instance), _i, _i, _i, _vp, _sz, _vp]),
     "hc_batched_autotune": (_i, [ctypes.POINTER(hc_instance), _i, _i, _vp, _sz, _i, _vp,
                                  ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)]),

@@ -53,7 +53,7 @@ static cudaError_t launch_chunk(const ChunkPlan& p, const UniformUnits& uu,
 
 template <class M>
 static cudaError_t chunk_forward_m(const ChunkPlan& p, const void* x, const void* y, void* z,
-                                   unsigned char* ws, cudaStream_t st) {
+                                   unsigned char* ws, cudaStream_t st, void* w_user) {
   typedef typename M::In In;
   typedef typename M::W W;
   constexpr bool kMixed = !std::is_same<typename M::W, typename M::Out>::value;
@@ -75,8 +75,11 @@ static cudaError_t chunk_forward_m(const ChunkPlan& p, const void* x, const void
   e = cudaMemsetAsync(ws, 0, p.off_ctr + 8 * (size_t)(p.units + 1), st);
   if (e != cudaSuccess) return e;
   const bool w_in_ws = kMixed && (p.m > 0 || p.ap > 0);
-  W* wbuf = w_in_ws ? (W*)(ws + p.off_w) : (W*)z;
-  const bool fin = kMixed && p.ap == 0;  // the columns finish the result
+  // split: the caller's array holds the intermediate and z only receives the
+  // final stores
+  const bool split = !kMixed && w_user != nullptr;
+  W* wbuf = w_in_ws ? (W*)(ws + p.off_w) : (split ? (W*)w_user : (W*)z);
+  const bool fin = (kMixed || split) && p.ap == 0;  // the columns finish the result
   UniformUnits uu;
   uu.x = X;
   uu.y = Y;
@@ -105,7 +108,7 @@ static cudaError_t chunk_forward_m(const ChunkPlan& p, const void* x, const void
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(p.ap - d0 - k) * (long long)pow3z(p.C + p.m);
     const bool last = i == p.n_interp - 1;
-    if (last && kMixed)
+    if (last && (kMixed || split))
       e = launch_interp<M, true>(k, p.cols, wbuf, z, hi, lo, st);
     else
       e = launch_interp<M, false>(k, p.cols, wbuf, wbuf, hi, lo, st);

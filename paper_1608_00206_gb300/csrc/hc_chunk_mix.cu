@@ -4,8 +4,8 @@
 namespace hc {
 
 cudaError_t chunk_forward_mix(const ChunkPlan& p, const void* x, const void* y, void* z,
-                            unsigned char* ws, cudaStream_t st) {
-  return chunk_forward_m<ModeMixed>(p, x, y, z, ws, st);
+                            unsigned char* ws, cudaStream_t st, void* w) {
+  return chunk_forward_m<ModeMixed>(p, x, y, z, ws, st, w);
 }
 
 }  // namespace hc

@@ -176,7 +176,7 @@ FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req) {
 
 template <class M>
 static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, void* z,
-                               unsigned char* ws, cudaStream_t st) {
+                               unsigned char* ws, cudaStream_t st, void* w_user) {
   typedef typename M::In In;
   typedef typename M::W W;
   const int D = p.D, C = p.C, a = p.a;
@@ -207,7 +207,9 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
   // K2
   const long long ntiles = (long long)pow3z(a);
   const bool mixed_ws = (sizeof(W) != sizeof(typename M::Out)) && a > 0;
-  W* Wbuf = mixed_ws ? (W*)(ws + p.off_w) : (W*)z;
+  // split: the caller's array holds the intermediate, z only the final stores
+  const bool split = !mixed_ws && w_user != nullptr && sizeof(W) == sizeof(typename M::Out);
+  W* Wbuf = mixed_ws ? (W*)(ws + p.off_w) : (split ? (W*)w_user : (W*)z);
   if (a == 0)
     e = launch_tile<M, true>(C, X, Y, z, ntiles, st);
   else
@@ -219,7 +221,7 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
     const bool last = (i == p.n_interp - 1);
-    if (last && mixed_ws)
+    if (last && (mixed_ws || split))
       e = launch_interp<M, true>(k, p.cols, Wbuf, z, hi, lo, st);
     else
       e = launch_interp<M, false>(k, p.cols, Wbuf, Wbuf, hi, lo, st);
@@ -309,23 +311,23 @@ ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
 }
 
 cudaError_t chunk_dispatch(const ChunkPlan& p, const void* x, const void* y, void* z,
-                           unsigned char* ws, cudaStream_t st) {
+                           unsigned char* ws, cudaStream_t st, void* w) {
   switch (p.dtype) {
-    case HC_INT64: return chunk_forward_i64(p, x, y, z, ws, st);
-    case HC_FP64: return chunk_forward_f64(p, x, y, z, ws, st);
-    case HC_FP32: return chunk_forward_f32(p, x, y, z, ws, st);
-    case HC_FP32_MIXED: return chunk_forward_mix(p, x, y, z, ws, st);
+    case HC_INT64: return chunk_forward_i64(p, x, y, z, ws, st, w);
+    case HC_FP64: return chunk_forward_f64(p, x, y, z, ws, st, w);
+    case HC_FP32: return chunk_forward_f32(p, x, y, z, ws, st, w);
+    case HC_FP32_MIXED: return chunk_forward_mix(p, x, y, z, ws, st, w);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, void* z,
-                             unsigned char* ws, cudaStream_t st) {
+                             unsigned char* ws, cudaStream_t st, void* w) {
   switch (p.dtype) {
-    case HC_INT64: return run_forward<ModeI64>(p, x, y, z, ws, st);
-    case HC_FP64: return run_forward<ModeF64>(p, x, y, z, ws, st);
-    case HC_FP32: return run_forward<ModeF32>(p, x, y, z, ws, st);
-    case HC_FP32_MIXED: return run_forward<ModeMixed>(p, x, y, z, ws, st);
+    case HC_INT64: return run_forward<ModeI64>(p, x, y, z, ws, st, w);
+    case HC_FP64: return run_forward<ModeF64>(p, x, y, z, ws, st, w);
+    case HC_FP32: return run_forward<ModeF32>(p, x, y, z, ws, st, w);
+    case HC_FP32_MIXED: return run_forward<ModeMixed>(p, x, y, z, ws, st, w);
   }
   return cudaErrorInvalidValue;
 }
@@ -382,7 +384,7 @@ size_t schedule_ws(int D, hc_dtype dtype, const hc_schedule& s) {
 
 hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtype dtype,
                            void* workspace, size_t ws_bytes, cudaStream_t stream,
-                           const hc_schedule* sched) {
+                           const hc_schedule* sched, void* w) {
   if (D < 0 || D > HC_MAX_D) return HC_ERR_ARG;
   const size_t es = elem_size(dtype);
   if (es == 0) return HC_ERR_DTYPE;
@@ -400,11 +402,17 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
       (overlaps(workspace, need, z, nz) || overlaps(workspace, need, x, nx) ||
        overlaps(workspace, need, y, nx)))
     return HC_ERR_ALIAS;
+  if (w) {
+    if (!aligned(w, 16)) return HC_ERR_ALIGN;
+    if (overlaps(w, nz, z, nz) || overlaps(w, nz, x, nx) || overlaps(w, nz, y, nx) ||
+        (workspace && need > 0 && overlaps(w, nz, workspace, need)))
+      return HC_ERR_ALIAS;
+  }
   if (s.kind == HC_SCHED_PASSES || D == 0)
-    return record_cuda_error(
-        forward_dispatch(passes_plan(D, dtype, s), x, y, z, (unsigned char*)workspace, stream));
-  return record_cuda_error(
-      chunk_dispatch(chunked_plan(D, dtype, s), x, y, z, (unsigned char*)workspace, stream));
+    return record_cuda_error(forward_dispatch(passes_plan(D, dtype, s), x, y, z,
+                                              (unsigned char*)workspace, stream, w));
+  return record_cuda_error(chunk_dispatch(chunked_plan(D, dtype, s), x, y, z,
+                                          (unsigned char*)workspace, stream, w));
 }
 
 // Candidate schedules of the autotuner for (D, dtype).
@@ -448,6 +456,37 @@ extern "C" hc_status hc_convolve_schedule(const void* x, const void* y, void* z,
                                           size_t ws_bytes, hc_stream_t stream) {
   if (!s) return HC_ERR_ARG;
   return hc::convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, (cudaStream_t)stream, s);
+}
+
+extern "C" hc_status hc_convolve_out(const void* x, const void* y, void* w, void* z, int D,
+                                     hc_dtype dtype, void* workspace, size_t ws_bytes,
+                                     hc_stream_t stream) {
+  if (dtype == HC_FP32_MIXED) {
+    if (w) return HC_ERR_ARG;  // its intermediate lives in the workspace
+  } else if (!w) {
+    return HC_ERR_ARG;
+  }
+  // The kernels store to z and w at these addresses: z must be device,
+  // managed or page-locked host memory mapped at the same address, w device
+  // or managed memory.  Checked on the host, before any launch.
+  if (!x || !y || !z) return HC_ERR_ARG;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, z) != cudaSuccess) {
+    cudaGetLastError();
+    return HC_ERR_ARG;
+  }
+  if (a.type == cudaMemoryTypeUnregistered ||
+      (a.type == cudaMemoryTypeHost && a.devicePointer != z))
+    return HC_ERR_ARG;
+  if (w) {
+    if (cudaPointerGetAttributes(&a, w) != cudaSuccess) {
+      cudaGetLastError();
+      return HC_ERR_ARG;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return HC_ERR_ARG;
+  }
+  return hc::convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, (cudaStream_t)stream,
+                              nullptr, w);
 }
 
 extern "C" hc_status hc_set_default_schedule(int D, hc_dtype dtype, const hc_schedule* s) {

@@ -47,27 +47,30 @@ struct ChunkPlan {
 ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req);
 
 cudaError_t chunk_forward_i64(const ChunkPlan& p, const void* x, const void* y, void* z,
-                              unsigned char* ws, cudaStream_t st);
+                              unsigned char* ws, cudaStream_t st, void* w = nullptr);
 cudaError_t chunk_forward_f64(const ChunkPlan& p, const void* x, const void* y, void* z,
-                              unsigned char* ws, cudaStream_t st);
+                              unsigned char* ws, cudaStream_t st, void* w = nullptr);
 cudaError_t chunk_forward_f32(const ChunkPlan& p, const void* x, const void* y, void* z,
-                              unsigned char* ws, cudaStream_t st);
+                              unsigned char* ws, cudaStream_t st, void* w = nullptr);
 cudaError_t chunk_forward_mix(const ChunkPlan& p, const void* x, const void* y, void* z,
-                              unsigned char* ws, cudaStream_t st);
+                              unsigned char* ws, cudaStream_t st, void* w = nullptr);
 
 // c_req, kmax_req <= 0 select the defaults (largest tile, 6 axes per pass).
 FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);
 
 cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, void* z,
-                             unsigned char* ws, cudaStream_t st);
+                             unsigned char* ws, cudaStream_t st, void* w = nullptr);
 
 // Validated schedule with kind resolved (1 = passes, 2 = chunked).
 bool schedule_valid(const hc_schedule& s, hc_dtype dtype);
 hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s);
 size_t schedule_ws(int D, hc_dtype dtype, const hc_schedule& s);
 
+// w: the caller's device array for the 3^D intermediate (nullptr: the
+// intermediate lives in z, or in the workspace for HC_FP32_MIXED); with w,
+// z is written only by the final stores.
 hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtype dtype,
                            void* workspace, size_t ws_bytes, cudaStream_t stream,
-                           const hc_schedule* sched);
+                           const hc_schedule* sched, void* w = nullptr);
 
 }  // namespace hc

@@ -32,6 +32,10 @@ def gpu_conv(hc, x, y, **kw):
     return z.cpu().numpy().reshape(-1)
 
 
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
 def bits(a):
     return a.view(np.uint64) if a.dtype.itemsize == 8 else a.view(np.uint32)
 
@@ -270,6 +274,89 @@ def test_host_buffers_end_to_end(hc):
     z = hc.convolve(xt, yt)
     assert not z.is_cuda and z.is_pinned()
     assert np.array_equal(z.numpy(), oracle.convolve(x, y))
+
+
+@pytest.mark.parametrize("kind,D,sched", [
+    ("int64", 13, None), ("int64", 14, (2, 8, 6, 0)), ("int64", 15, (2, 4, 4, -32)),
+    ("int64", 14, (1, 7, 6, 16)), ("float64", 12, None), ("float32", 16, None),
+    ("float32", 13, (2, 8, 3, 0)), ("mixed", 12, None), ("mixed", 13, (2, 8, 5, 0))])
+def test_final_stores_into_pinned_host_memory(hc, kind, D, sched):
+    """hc_convolve_out: the intermediate in a device array, the final stores
+    (last whole-array pass, or the chunk's column tickets when no outer pass
+    follows, or the tile when there is neither) straight into page-locked
+    host memory; bitwise the oracle's result, for the default and for forced
+    schedules (installed as the default, since hc_convolve_out takes it)."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib
+    if kind == "int64":
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=D)
+        want = oracle.convolve(x, y, threads=8)
+    elif kind == "mixed":
+        x, y = inputs.uniform01_pair(D, seed=D)
+        want = oracle.convolve_mixed(x, y)
+    else:
+        x, y = inputs.normal_pair(D, seed=D, dtype=np.float64 if kind == "float64" else np.float32)
+        want = oracle.convolve(x, y, threads=8)
+    code = {"int64": _lib.HC_INT64, "float64": _lib.HC_FP64, "float32": _lib.HC_FP32,
+            "mixed": _lib.HC_FP32_MIXED}[kind]
+    xt = torch.from_numpy(x).pin_memory()
+    yt = torch.from_numpy(y).pin_memory()
+    hc.convolve(xt.to(DEV), yt.to(DEV))  # installs the shipped table, as any first call does
+    lib = _lib.lib()
+    saved = _lib.hc_schedule()
+    assert lib.hc_get_default_schedule(D, code, ctypes.byref(saved)) == 0
+    if sched is not None:
+        s = _lib.hc_schedule(*sched)
+        assert lib.hc_set_default_schedule(D, code, ctypes.byref(s)) == 0
+    from paper_1608_00206_gb300 import api
+    threshold = api._DIRECT_HOST_BYTES
+    api._DIRECT_HOST_BYTES = 0  # this size goes through the final-store path too
+    try:
+        z = hc.convolve(xt, yt, mixed=(kind == "mixed"))
+    finally:
+        api._DIRECT_HOST_BYTES = threshold
+        assert lib.hc_set_default_schedule(D, code, ctypes.byref(saved)) == 0
+    assert not z.is_cuda and z.is_pinned()
+    assert_bit_equal(z.numpy().reshape(-1), want)
+
+
+def test_convolve_out_device_arrays_and_argument_checks(hc):
+    """hc_convolve_out with device z and w gives hc_convolve's bits; a null or
+    misplaced intermediate, an output the device cannot store to (pageable
+    host memory) and overlapping arrays are rejected on the host, before any
+    launch."""
+    from paper_1608_00206_gb300 import _lib
+    lib = _lib.lib()
+    D = 12
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=3)
+    xd, yd = T(x), T(y)
+    z = torch.empty(3 ** D, dtype=torch.int64, device=DEV)
+    w = torch.empty(3 ** D, dtype=torch.int64, device=DEV)
+    nb = int(lib.hc_workspace_size(D, _lib.HC_INT64))
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=DEV)
+    st = torch.cuda.current_stream().cuda_stream
+    args = (D, _lib.HC_INT64, ws.data_ptr(), nb, st)
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), w.data_ptr(), z.data_ptr(), *args) == 0
+    torch.cuda.synchronize()
+    assert_bit_equal(z.cpu().numpy(), oracle.convolve(x, y))
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), None, z.data_ptr(), *args) == \
+        _lib.HC_ERR_ARG
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), z.data_ptr(), z.data_ptr(), *args) == \
+        _lib.HC_ERR_ALIAS
+    pageable = np.empty(3 ** D, np.int64)  # not known to the CUDA runtime
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), w.data_ptr(),
+                               pageable.ctypes.data, *args) == _lib.HC_ERR_ARG
+    pinned_w = torch.empty(3 ** D, dtype=torch.int64).pin_memory()  # w must be device memory
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), pinned_w.data_ptr(), z.data_ptr(),
+                               *args) == _lib.HC_ERR_ARG
+    zf = torch.empty(3 ** D, dtype=torch.float32, device=DEV)
+    xf, yf = T(x.astype(np.float32)), T(y.astype(np.float32))
+    nbm = int(lib.hc_workspace_size(D, _lib.HC_FP32_MIXED))
+    wsm = torch.empty(max(nbm, 256), dtype=torch.uint8, device=DEV)
+    assert lib.hc_convolve_out(xf.data_ptr(), yf.data_ptr(), w.data_ptr(), zf.data_ptr(), D,
+                               _lib.HC_FP32_MIXED, wsm.data_ptr(), nbm, st) == _lib.HC_ERR_ARG
+    torch.cuda.synchronize()
 
 
 def test_shaped_input_gives_shaped_output(hc):
