@@ -62,6 +62,7 @@ def _lib():
             lib.oracle_points.argtypes = [vp, vp, i, i, vp, sz, vp]
             lib.oracle_recurrence.argtypes = [vp, vp, vp, i, i, i, i]
             lib.oracle_recurrence_mixed.argtypes = [vp, vp, vp, i]
+            lib.oracle_recurrence_inplace.argtypes = [vp, vp, vp, i, i, i]
             lib.oracle_adjoint.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_adjoint_brute.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_zabs.argtypes = [vp, vp, vp, i]
@@ -132,6 +133,22 @@ def convolve(x, y, direct_last_axis: bool = False, threads: int = 1) -> np.ndarr
                                 int(threads)):
         raise RuntimeError("oracle_recurrence failed")
     return z
+
+
+def convolve_inplace(x, y, save: bool = True):
+    """The in-place schedule (sums formed in the first halves of x and y,
+    put back before each call returns): returns (z, x_after, y_after).
+    save=True copies the first halves aside (exact for every type);
+    save=False subtracts again (exact for int64 only)."""
+    x = np.array(x, copy=True).reshape(-1)
+    y = np.array(y, copy=True).reshape(-1)
+    x, y, D, code = _prep(x, y)
+    x = np.array(x, copy=True)
+    y = np.array(y, copy=True)
+    z = np.empty(3 ** D, dtype=x.dtype)
+    if _lib().oracle_recurrence_inplace(_ptr(x), _ptr(y), _ptr(z), D, code, int(save)):
+        raise RuntimeError("oracle_recurrence_inplace failed")
+    return z, x, y
 
 
 def convolve_mixed(x, y) -> np.ndarray:

@@ -128,6 +128,53 @@ void rec(const T* x, const T* y, T* z, int D, bool direct, T* scratch) {
   for (size_t k = 0; k < n; ++k) z[n + k] = (z[n + k] - z[k]) - z[2 * n + k];
 }
 
+// The paper's in-place schedule done correctly (Methods; the memory pairing
+// that Algorithm 2 is built on): z[0] and z[2] first, then the sums formed
+// in place in the first halves of x and y (no fresh temporaries), the middle
+// sub-problem on them, and the first halves put back before returning, so
+// every call leaves its inputs as it found them (the listing forgets this,
+// and its later sums read transformed data).  Putting back:
+//   save = true : copy the first halves aside before summing (2^(D-1) each
+//                 on the current path: O(2^D) in all) and copy them back --
+//                 exact for every type, the same operations as rec();
+//   save = false: subtract the second half again, x[k] = (x[k]+x[h+k]) -
+//                 x[h+k] -- no scratch, exact in Z/2^64 only (in floating
+//                 point the restored first halves are off by the rounding of
+//                 the sum, which the paper's exactness condition (a+b)-a = b
+//                 rules out).
+// The output is formed in z exactly as in rec(); x and y are modified
+// during the call.
+template <class T>
+void rec_inplace(T* x, T* y, T* z, int D, bool save, T* saved) {
+  if (D == 0) {
+    z[0] = x[0] * y[0];
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  rec_inplace(x, y, z, D - 1, save, saved);                  // z[0] = x[0]*y[0]
+  rec_inplace(x + h, y + h, z + 2 * n, D - 1, save, saved);  // z[2] = x[1]*y[1]
+  if (save) {
+    memcpy(saved, x, h * sizeof(T));
+    memcpy(saved + h, y, h * sizeof(T));
+  }
+  for (size_t k = 0; k < h; ++k) {
+    x[k] = x[k] + x[h + k];
+    y[k] = y[k] + y[h + k];
+  }
+  rec_inplace(x, y, z + n, D - 1, save, saved + 2 * h);      // t
+  if (save) {
+    memcpy(x, saved, h * sizeof(T));
+    memcpy(y, saved + h, h * sizeof(T));
+  } else {
+    for (size_t k = 0; k < h; ++k) {
+      x[k] = x[k] - x[h + k];
+      y[k] = y[k] - y[h + k];
+    }
+  }
+  for (size_t k = 0; k < n; ++k) z[n + k] = (z[n + k] - z[k]) - z[2 * n + k];
+}
+
 // Same recurrence with the three sub-problems of the top `par_levels` levels
 // run as OpenMP tasks.  Every element sees the same operations in the same
 // order as rec(), so the result is bitwise identical.
@@ -334,6 +381,19 @@ int oracle_recurrence(const void* x, const void* y, void* z, int D, int dtype, i
     case 0: rec_top((const u64*)x, (const u64*)y, (u64*)z, D, direct != 0, threads); return 0;
     case 1: rec_top((const double*)x, (const double*)y, (double*)z, D, direct != 0, threads); return 0;
     case 2: rec_top((const float*)x, (const float*)y, (float*)z, D, direct != 0, threads); return 0;
+  }
+  return 1;
+}
+
+// In-place schedule; x and y are modified during the call and handed back
+// (exactly with save != 0, or for int64).
+int oracle_recurrence_inplace(void* x, void* y, void* z, int D, int dtype, int save) {
+  const size_t es = dtype == 0 || dtype == 1 ? 8 : 4;
+  std::vector<unsigned char> saved(save ? es * ((size_t)2 << D) + 16 : 16);
+  switch (dtype) {
+    case 0: rec_inplace((u64*)x, (u64*)y, (u64*)z, D, save != 0, (u64*)saved.data()); return 0;
+    case 1: rec_inplace((double*)x, (double*)y, (double*)z, D, save != 0, (double*)saved.data()); return 0;
+    case 2: rec_inplace((float*)x, (float*)y, (float*)z, D, save != 0, (float*)saved.data()); return 0;
   }
   return 1;
 }

@@ -218,6 +218,56 @@ def test_separable_probability_fp64(oracle, D):
     assert abs(z.sum() - 1.0) < 1e-12
 
 
+# ------------------------------------------- in-place schedule (Methods)
+
+
+@pytest.mark.parametrize("D", list(range(0, 10)))
+def test_inplace_schedule_int64_vs_brute(oracle, D):
+    """The corrected in-place schedule (sums in the first halves of x and y,
+    put back before each call returns) equals brute force in Z/2^64 with
+    either way of putting back, and hands x and y back unchanged."""
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=50 + D)
+    want = oracle.brute_force(x, y)
+    for save in (True, False):
+        z, xa, ya = oracle.convolve_inplace(x, y, save=save)
+        assert np.array_equal(z, want), save
+        assert np.array_equal(xa, x) and np.array_equal(ya, y), save
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_inplace_schedule_with_saved_halves_is_the_recurrence(oracle, dt):
+    """With the first halves copied aside, every element sees the
+    recurrence's operations in its order: the result is bitwise the fresh-
+    temporary recurrence's, exact on dyadic inputs within the forward bound,
+    and x, y come back bitwise."""
+    D = 10
+    x, y = inputs.normal_pair(D, seed=5, dtype=dt)
+    z, xa, ya = oracle.convolve_inplace(x, y, save=True)
+    assert np.array_equal(z.view(np.uint8), oracle.convolve(x, y).view(np.uint8))
+    assert np.array_equal(xa.view(np.uint8), x.view(np.uint8))
+    assert np.array_equal(ya.view(np.uint8), y.view(np.uint8))
+
+
+def test_inplace_schedule_subtracting_back_needs_exact_sums(oracle):
+    """Putting the first halves back by subtraction is exact only when
+    (a + b) - b = a (the paper's exactness condition): with a half that the
+    sum absorbs (0.1 next to 1e17) x comes back changed, and the result
+    departs from the recurrence; with integer-valued inputs, whose sums are
+    all exact, it is the recurrence bit for bit."""
+    D = 3
+    x = np.array([0.1, 0.2, 0.3, 0.4, 1e17, 1e17, 1e17, 1e17])
+    y = np.arange(1.0, 9.0)
+    z, xa, _ = oracle.convolve_inplace(x, y, save=False)
+    assert not np.array_equal(xa, x)
+    assert xa[0] == 0.0  # (0.1 + 1e17) - 1e17
+    zr, _, _ = oracle.convolve_inplace(x, y, save=True)
+    assert not np.array_equal(z, zr)
+    xi, yi = inputs.uniform_int_pair(10, -1000, 1000, seed=4)
+    xs, ys = xi.astype(np.float64), yi.astype(np.float64)  # every sum exact
+    z, xa, ya = oracle.convolve_inplace(xs, ys, save=False)
+    assert np.array_equal(z, oracle.convolve(xs, ys)) and np.array_equal(xa, xs)
+
+
 def test_direct_last_axis_is_a_different_rounding(oracle):
     """Integers: identical; floats: the D = 1 base case rounds differently but
     stays within the same bound."""
