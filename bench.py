@@ -420,13 +420,27 @@ def _time_steps(wl, steps, warmup, dist):
         _lib.lib().hc_profile_enable(0)
         eager = _lib.profile_collect()
         prof = {k: (v[0] * steps, v[1] * steps) for k, v in eager.items()}
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=wl.dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = _max_over_ranks(ms, dist, wl.dev)
     torch.cuda.synchronize()
     return ms, prof, clk
+
+
+def _max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it), then a barrier; ms itself
+    with one rank.  Replicas run the same work, so the whole job's throughput
+    is world x per-rank work / this time."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def _whole_job_value(world, outputs_per_step, steps, ms):
+    """Outputs per second over all ranks for `steps` steps in `ms`."""
+    return world * outputs_per_step * steps / (ms / 1e3)
 
 
 def _comparisons(wl, ms_per_step):
@@ -706,7 +720,7 @@ def main():
     if args.workload == "d10_int64":
         wl.use_graph()  # launch-bound: replay the convolution from a CUDA graph
     ms, prof, clk = _time_steps(wl, args.steps, args.warmup, dist)
-    value = world * wl.outputs * args.steps / (ms / 1e3)
+    value = _whole_job_value(world, wl.outputs, args.steps, ms)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     peak_hbm, peak_kind = _peaks()
