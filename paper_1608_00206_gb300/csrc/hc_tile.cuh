@@ -74,7 +74,10 @@ struct TileSmem {
   static constexpr size_t kW = sizeof(W) * (size_t)p3(C);
   // transposed buffer feeding the fused stage, per operand
   static constexpr size_t kLast = sizeof(In) * (size_t)p2(TileShape<C>::gL) * p3(C - TileShape<C>::gL);
-  static constexpr size_t kS1 = TileShape<C>::G == 3 ? 2 * sizeof(In) * (size_t)p3(TileShape<C>::g0) * p2(C - TileShape<C>::g0) : 0;
+  // stage-0 output [operand][3^g0][S1R]: rows padded so that the stage-1
+  // reads of two neighbouring rows fall in different banks
+  static constexpr int S1R = p2(C - TileShape<C>::g0) + (p2(C - TileShape<C>::g0) % 16 == 0 ? 8 : 0);
+  static constexpr size_t kS1 = TileShape<C>::G == 3 ? 2 * sizeof(In) * (size_t)p3(TileShape<C>::g0) * S1R : 0;
   static_assert(kS1 <= kW, "stage-0 buffer must fit inside the W tile");
   // With at most 256 fused pencils (one per thread of a 256-thread CTA) the
   // fused stage reads all its inputs before any thread writes W, so the
@@ -189,9 +192,10 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
 #pragma unroll
             for (int j = 0; j < p3(S::g0); ++j) d[r * p3(S::g0) + j] = v[j];
           } else {
-            In* d = S1 + op * (p3(S::g0) * R);
+            constexpr int S1R = TileSmem<M, C>::S1R;
+            In* d = S1 + op * (p3(S::g0) * S1R);
 #pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) d[j * R + r] = v[j];
+            for (int j = 0; j < p3(S::g0); ++j) d[j * S1R + r] = v[j];
           }
         }
       }
@@ -201,14 +205,15 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
         constexpr int O = p3(S::g0);
         constexpr int R = p2(S::gL);  // remaining binary axes (innermost group)
         constexpr int NP = O * R;
+        constexpr int S1R = TileSmem<M, C>::S1R;  // = 8 * R + padding
         #pragma unroll 1
         for (int p = tid; p < 2 * NP; p += nt) {
           const int op = p / NP, q = p - op * NP;
           const int o = q / R, r = q - o * R;
-          const In* s = S1 + op * (O * 8 * R);
+          const In* s = S1 + op * (O * S1R);
           In v[27];
 #pragma unroll
-          for (int b = 0; b < 8; ++b) v[b] = s[(o * 8 + b) * R + r];
+          for (int b = 0; b < 8; ++b) v[b] = s[o * S1R + b * R + r];
           eval_pencil<M, 3>(v);
           In* d = op ? LastY : LastX;
 #pragma unroll
