@@ -675,8 +675,8 @@ def main():
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
-                    help="force a schedule kind:c:k:cols (kind passes|chunked) instead of the "
-                         "tuned default, e.g. passes:6:6:32")
+                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked) "
+                         "instead of the tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
     if args.D is not None and args.workload not in SINGLE:
         ap.error("--D applies to single-instance workloads only")
@@ -710,9 +710,11 @@ def main():
     if args.schedule:
         if args.workload not in SINGLE:
             ap.error("--schedule applies to single-instance workloads only")
-        kind, c, k, cols = args.schedule.split(":")
+        kind, c, k, cols, *outer = args.schedule.split(":")
         wl.sched = {"c": int(c), "cols": int(cols),
                     ("m" if kind == "chunked" else "kmax"): int(k)}
+        if outer:
+            wl.sched["cols_outer"] = int(outer[0])
         if kind not in ("passes", "chunked"):
             ap.error("schedule kind is passes or chunked")
         nb = wl.hc.workspace_size(wl.D, wl.z.dtype, wl.mixed, **wl.sched)

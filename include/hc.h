@@ -124,7 +124,10 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  * D); k in 0..6 (0 = 6); cols = columns per whole-array interpolation tile,
  * 8, 16 or 32, each element copied on its own (0 = 32 for 4-byte and 16 for
  * 8-byte intermediates), or -16 / -32: 16 or 32 columns whose rows are copied
- * in 16-byte pieces (each row widened to 16-byte boundaries).
+ * in 16-byte pieces (each row widened to 16-byte boundaries).  cols_outer:
+ * the same choice for the whole-array pass over the outermost axes alone
+ * (its rows are the farthest apart; 0 = cols).  The adjoint's transposed
+ * passes take the default schedule's widths for the same (D, dtype).
  * HC_ERR_ARG for fields out of range. */
 #define HC_SCHED_DEFAULT 0
 #define HC_SCHED_PASSES 1
@@ -135,6 +138,7 @@ typedef struct {
   int c;
   int k;
   int cols;
+  int cols_outer;  /* width of the pass over the outermost axes; 0 = cols */
 } hc_schedule;
 
 size_t hc_workspace_size_schedule(int D, hc_dtype dtype, const hc_schedule* s);

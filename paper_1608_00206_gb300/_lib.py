@@ -23,10 +23,11 @@ HC_SCHED_DEFAULT, HC_SCHED_PASSES, HC_SCHED_CHUNKED = 0, 1, 2
 
 
 class hc_schedule(ctypes.Structure):
-    _fields_ = [("kind", _i), ("c", _i), ("k", _i), ("cols", _i)]
+    _fields_ = [("kind", _i), ("c", _i), ("k", _i), ("cols", _i), ("cols_outer", _i)]
 
     def as_dict(self):
-        return {"kind": self.kind, "c": self.c, "k": self.k, "cols": self.cols}
+        return {"kind": self.kind, "c": self.c, "k": self.k, "cols": self.cols,
+                "cols_outer": self.cols_outer}
 
 
 class hc_instance(ctypes.Structure):

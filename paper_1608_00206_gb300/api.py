@@ -48,23 +48,24 @@ def _out_shape(x: torch.Tensor, D: int):
     return (3,) * D if (x.dim() == D and all(s == 2 for s in x.shape) and D > 0) else (3 ** D,)
 
 
-def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0):
+def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: int = 0):
     """None for the default schedule; else an hc_schedule: m > 0 selects the
     chunked schedule (c tile axes, m middle axes), otherwise c or kmax select
     the whole-array-pass schedule; cols alone keeps the default kind."""
     if m:
-        return _lib.hc_schedule(_lib.HC_SCHED_CHUNKED, c, m, cols)
+        return _lib.hc_schedule(_lib.HC_SCHED_CHUNKED, c, m, cols, cols_outer)
     if c or kmax:
-        return _lib.hc_schedule(_lib.HC_SCHED_PASSES, c, kmax, cols)
-    if cols:
-        return _lib.hc_schedule(_lib.HC_SCHED_DEFAULT, 0, 0, cols)
+        return _lib.hc_schedule(_lib.HC_SCHED_PASSES, c, kmax, cols, cols_outer)
+    if cols or cols_outer:
+        return _lib.hc_schedule(_lib.HC_SCHED_DEFAULT, 0, 0, cols, cols_outer)
     return None
 
 
 def workspace_size(D: int, dtype: torch.dtype = torch.float32, mixed: bool = False,
-                   c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0) -> int:
+                   c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0,
+                   cols_outer: int = 0) -> int:
     code = _code(dtype, mixed)
-    s = _schedule(c, kmax, m, cols)
+    s = _schedule(c, kmax, m, cols, cols_outer)
     if s is None:
         # the default schedule is the tuned one once the table is installed
         if torch.cuda.is_available():
@@ -114,14 +115,16 @@ _DIRECT_HOST_BYTES = 8 << 30
 
 def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, *,
              mixed: bool = False, workspace: torch.Tensor | None = None, stream=None,
-             c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0) -> torch.Tensor:
+             c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0,
+             cols_outer: int = 0) -> torch.Tensor:
     """z = x * y over {0,1,2}^D.
 
     CUDA tensors: runs on their device and the current (or given) stream,
     asynchronously.  Schedules: default (hc_convolve); m > 0 selects the
     chunked schedule with m middle axes and c tile axes; otherwise c or kmax
     select the whole-array-pass schedule; cols sets the interpolation tile
-    width.  CPU tensors (the end-to-end path): x and y are copied to
+    width (cols_outer: that of the pass over the outermost axes).  CPU
+    tensors (the end-to-end path): x and y are copied to
     the current CUDA device and convolved there; z is computed on the device
     and copied back into `out` (a new CPU tensor, pinned when x is), except
     that an output above 8 GiB going to a page-locked `out` is stored
@@ -132,7 +135,7 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
         raise ValueError("x and y must have the same dtype and size")
     D = dim_of(x)
     code = _code(x.dtype, mixed)
-    sched = _schedule(c, kmax, m, cols)
+    sched = _schedule(c, kmax, m, cols, cols_outer)
     if x.is_cuda:
         if not y.is_cuda or y.device != x.device:
             raise ValueError("x and y must be on the same CUDA device")

@@ -486,13 +486,15 @@ static cudaError_t run_backward(const BwdPlan& p, const void* dz, const void* x,
   // I^T on the outer axes: dz -> G (the first pass copies out of dz).  The
   // passes have the shape of the forward's whole-array passes for the same
   // (D, dtype), so they take the tile width of its default schedule.
-  const int cols = resolve_schedule(D, p.dtype, nullptr).cols;
+  const hc_schedule fs = resolve_schedule(D, p.dtype, nullptr);
   const W* G = (const W*)dz;
   W* Gbuf = (W*)(ws + p.off_g);
   for (int i = 0; i < p.n_it; ++i) {
     const int d0 = p.it_d0[i], k = p.it_k[i];
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
+    // the pass over the outermost axes (d0 = 0) takes the outer width
+    const int cols = d0 == 0 && p.n_it >= 2 && fs.cols_outer ? fs.cols_outer : fs.cols;
     e = launch_interp<M, false, true>(k, cols, G, Gbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
     G = Gbuf;

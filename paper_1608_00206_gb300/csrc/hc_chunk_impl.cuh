@@ -108,10 +108,11 @@ static cudaError_t chunk_forward_m(const ChunkPlan& p, const void* x, const void
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(p.ap - d0 - k) * (long long)pow3z(p.C + p.m);
     const bool last = i == p.n_interp - 1;
+    const int cols = last && p.cols_outer ? p.cols_outer : p.cols;  // outermost axes: hi = 1
     if (last && (kMixed || split))
-      e = launch_interp<M, true>(k, p.cols, wbuf, z, hi, lo, st);
+      e = launch_interp<M, true>(k, cols, wbuf, z, hi, lo, st);
     else
-      e = launch_interp<M, false>(k, p.cols, wbuf, wbuf, hi, lo, st);
+      e = launch_interp<M, false>(k, cols, wbuf, wbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -221,10 +221,12 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
     const bool last = (i == p.n_interp - 1);
+    // the last pass is the one over the outermost axes (hi = 1)
+    const int cols = last && p.cols_outer ? p.cols_outer : p.cols;
     if (last && (mixed_ws || split))
-      e = launch_interp<M, true>(k, p.cols, Wbuf, z, hi, lo, st);
+      e = launch_interp<M, true>(k, cols, Wbuf, z, hi, lo, st);
     else
-      e = launch_interp<M, false>(k, p.cols, Wbuf, Wbuf, hi, lo, st);
+      e = launch_interp<M, false>(k, cols, Wbuf, Wbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -347,19 +349,22 @@ bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
   const int cmax = dtype == HC_FP32 ? 9 : 8;
   if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_CHUNKED) return false;
   if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
-  return s.cols == 0 || s.cols == 8 || s.cols == 16 || s.cols == 32 || s.cols == -16 ||
-         s.cols == -32;
+  auto width_ok = [](int w) {
+    return w == 0 || w == 8 || w == 16 || w == 32 || w == -16 || w == -32;
+  };
+  return width_ok(s.cols) && width_ok(s.cols_outer);
 }
 
 hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
   if (s && s->kind != HC_SCHED_DEFAULT) return *s;
-  hc_schedule r = {HC_SCHED_CHUNKED, 0, 0, 0};
+  hc_schedule r = {HC_SCHED_CHUNKED, 0, 0, 0, 0};
   if (D >= 0 && D <= HC_MAX_D && dtype >= 0 && dtype < 4) {
     std::lock_guard<std::mutex> g(g_sched_mu);
     if (g_has_default[D][dtype]) r = g_default[D][dtype];
   }
-  if (s) {  // a DEFAULT schedule may still fix the column width
+  if (s) {  // a DEFAULT schedule may still fix the column widths
     if (s->cols) r.cols = s->cols;
+    if (s->cols_outer) r.cols_outer = s->cols_outer;
   }
   return r;
 }
@@ -367,12 +372,14 @@ hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
 static FwdPlan passes_plan(int D, hc_dtype dt, const hc_schedule& s) {
   FwdPlan p = make_fwd_plan(D, dt, s.c, s.k);
   p.cols = s.cols;
+  p.cols_outer = s.cols_outer;
   return p;
 }
 
 static ChunkPlan chunked_plan(int D, hc_dtype dt, const hc_schedule& s) {
   ChunkPlan p = make_chunk_plan(D, dt, s.c, s.k);
   p.cols = s.cols;
+  p.cols_outer = s.cols_outer;
   return p;
 }
 
@@ -420,15 +427,15 @@ static std::vector<hc_schedule> tune_candidates(int D, hc_dtype dtype) {
   std::vector<hc_schedule> v;
   const int cmax = dtype == HC_FP32 ? 9 : 8;
   if (D <= cmax) {
-    v.push_back({HC_SCHED_CHUNKED, 0, 0, 0});
+    v.push_back({HC_SCHED_CHUNKED, 0, 0, 0, 0});
     return v;
   }
   const int cols[5] = {8, 16, 32, -16, -32};
   for (int c = cmax - 1; c <= cmax; ++c) {
     for (int k = 3; k <= 6; ++k)
       for (int ci = 0; ci < 5; ++ci) {
-        v.push_back({HC_SCHED_PASSES, c, k, cols[ci]});
-        v.push_back({HC_SCHED_CHUNKED, c, k, cols[ci]});
+        v.push_back({HC_SCHED_PASSES, c, k, cols[ci], 0});
+        v.push_back({HC_SCHED_CHUNKED, c, k, cols[ci], 0});
       }
   }
   return v;
@@ -524,7 +531,7 @@ extern "C" hc_status hc_autotune(const void* x, const void* y, void* z, int D, h
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   if (ce != cudaSuccess) return record_cuda_error(ce);
-  hc_schedule win = {HC_SCHED_CHUNKED, 0, 0, 0};
+  hc_schedule win = {HC_SCHED_CHUNKED, 0, 0, 0, 0};
   double win_ms = -1.0;
   hc_status status = HC_OK;
   for (const hc_schedule& s : tune_candidates(D, dtype)) {
@@ -549,6 +556,39 @@ extern "C" hc_status hc_autotune(const void* x, const void* y, void* z, int D, h
     if (win_ms < 0.0 || t_min < win_ms) {
       win_ms = t_min;
       win = s;
+    }
+  }
+  // second stage: the winner's (kind, c, k) with every pair of widths for the
+  // inner passes and the pass over the outermost axes (meaningful when its
+  // plan has two or more whole-array passes)
+  if (status == HC_OK && win_ms >= 0.0 && win.kind == HC_SCHED_PASSES &&
+      passes_plan(D, dtype, win).n_interp >= 2) {
+    const int widths[5] = {8, 16, 32, -16, -32};
+    const hc_schedule base = win;
+    for (int wi = 0; wi < 25 && status == HC_OK; ++wi) {
+      hc_schedule s = base;
+      s.cols = widths[wi / 5];
+      s.cols_outer = widths[wi % 5];
+      if (s.cols == s.cols_outer) continue;  // a single width was timed already
+      status = convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, st, &s);  // warm-up
+      double t_min = -1.0;
+      for (int r = 0; r < reps && status == HC_OK; ++r) {
+        cudaEventRecord(e0, st);
+        status = convolve_checked(x, y, z, D, dtype, workspace, ws_bytes, st, &s);
+        cudaEventRecord(e1, st);
+        ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+          status = record_cuda_error(ce);
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (t_min < 0.0 || ms < t_min) t_min = ms;
+      }
+      if (status == HC_OK && t_min >= 0.0 && t_min < win_ms) {
+        win_ms = t_min;
+        win = s;
+      }
     }
   }
   cudaEventDestroy(e0);

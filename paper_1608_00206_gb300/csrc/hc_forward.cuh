@@ -17,7 +17,8 @@ struct FwdPlan {
   int interp_d0[HC_MAX_D], interp_k[HC_MAX_D];
   size_t off_xo, off_yo, off_tx, off_ty, off_w;
   size_t ws_bytes;
-  int cols;  // columns per whole-array interpolation tile (0 = default)
+  int cols;        // columns per whole-array interpolation tile (0 = default)
+  int cols_outer;  // the same for the pass over the outermost axes (0 = cols)
 };
 
 // The default schedule ("chunked"): the a' = D - C - m outermost axes are
@@ -40,7 +41,8 @@ struct ChunkPlan {
   size_t smem;
   size_t off_ctr, off_xo, off_yo, off_tx, off_ty, off_w;
   size_t ws_bytes;
-  int cols;  // columns per whole-array interpolation tile (0 = default)
+  int cols;        // columns per whole-array interpolation tile (0 = default)
+  int cols_outer;  // the same for the pass over the outermost axes (0 = cols)
 };
 
 // c_req: tile axes (0 = default); m_req: middle axes per chunk (0 = default).

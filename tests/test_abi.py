@@ -60,7 +60,7 @@ def test_default_schedule_table(L):
     assert L.hc_set_default_schedule(20, _lib.HC_INT64, ctypes.byref(s)) == 0
     try:
         assert L.hc_get_default_schedule(20, _lib.HC_INT64, ctypes.byref(got)) == 0
-        assert got.as_dict() == {"kind": 1, "c": 8, "k": 6, "cols": 16}
+        assert got.as_dict() == {"kind": 1, "c": 8, "k": 6, "cols": 16, "cols_outer": 0}
         assert L.hc_workspace_size(20, _lib.HC_INT64) == \
             L.hc_workspace_size_schedule(20, _lib.HC_INT64, ctypes.byref(s))
         assert L.hc_workspace_size(19, _lib.HC_INT64) != 0  # other entries untouched
@@ -123,13 +123,13 @@ def test_argument_errors_caught_on_host(L):
     assert conv(x, y, zz, 20, _lib.HC_INT64, zz, big, None) == _lib.HC_ERR_ALIAS
     # explicit schedules out of range
     for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (3, 0, 0, 0), (1, 0, 0, 12), (-1, 0, 0, 0),
-                (1, 0, 0, -8), (2, 0, 0, -64)]:
+                (1, 0, 0, -8), (2, 0, 0, -64), (1, 8, 6, 16, 12), (1, 8, 6, 16, -8)]:
         s = _lib.hc_schedule(*bad)
         assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, ctypes.byref(s), ws, size,
                                       None) == _lib.HC_ERR_ARG
         assert L.hc_set_default_schedule(10, _lib.HC_INT64, ctypes.byref(s)) == _lib.HC_ERR_ARG
     # 16-byte row copies are a valid tile width
-    for good in [(1, 8, 6, -16), (2, 8, 6, -32)]:
+    for good in [(1, 8, 6, -16), (2, 8, 6, -32), (1, 8, 6, 16, 32), (1, 8, 6, 32, -16)]:
         s = _lib.hc_schedule(*good)
         assert L.hc_set_default_schedule(10, _lib.HC_INT64, ctypes.byref(s)) == _lib.HC_OK
     assert L.hc_set_default_schedule(10, _lib.HC_INT64, None) == _lib.HC_OK

@@ -78,7 +78,7 @@ def test_adjoint_every_tile_width(hc, dt, cols):
     lib = _lib.lib()
     saved = _lib.hc_schedule()
     assert lib.hc_get_default_schedule(D, code, ctypes.byref(saved)) == 0
-    s = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 6, cols)
+    s = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 6, cols, -cols if cols in (16, 32) else 0)
     assert lib.hc_set_default_schedule(D, code, ctypes.byref(s)) == 0
     try:
         dx, dy = gpu_adj(hc, dz, x, y)
@@ -86,6 +86,30 @@ def test_adjoint_every_tile_width(hc, dt, cols):
         assert lib.hc_set_default_schedule(D, code, ctypes.byref(saved)) == 0
     wx, wy = oracle.adjoint(dz, x, y)
     assert np.array_equal(bits(dx), bits(wx)) and np.array_equal(bits(dy), bits(wy))
+
+
+@pytest.mark.parametrize("cols,cols_outer", [(16, -32), (32, 8)])
+def test_adjoint_outermost_pass_width(hc, cols, cols_outer):
+    """D = 16: eight outer axes, two transposed passes; the one over the
+    outermost axes takes the default schedule's cols_outer."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib
+    D = 16
+    x, y = inputs.uniform_int_pair(D, -100, 100, seed=9)
+    dz = np.random.default_rng(9).integers(-100, 101, size=3 ** D, dtype=np.int64)
+    hc.convolve(T(x), T(y))
+    lib = _lib.lib()
+    saved = _lib.hc_schedule()
+    assert lib.hc_get_default_schedule(D, _lib.HC_INT64, ctypes.byref(saved)) == 0
+    s = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 4, cols, cols_outer)
+    assert lib.hc_set_default_schedule(D, _lib.HC_INT64, ctypes.byref(s)) == 0
+    try:
+        dx, dy = gpu_adj(hc, dz, x, y)
+    finally:
+        assert lib.hc_set_default_schedule(D, _lib.HC_INT64, ctypes.byref(saved)) == 0
+    wx, wy = oracle.adjoint(dz, x, y)
+    assert np.array_equal(dx, wx) and np.array_equal(dy, wy)
 
 
 def test_one_sided(hc):

@@ -154,6 +154,25 @@ def test_every_interpolation_tile_width(hc, kind, cols):
         assert_bit_equal(gpu_conv(hc, x, y, mixed=(kind == "mixed"), c=c, kmax=kmax, cols=cols), want)
 
 
+@pytest.mark.parametrize("cols,cols_outer", [(16, 32), (32, 16), (16, -32), (-32, 8), (8, -16)])
+@pytest.mark.parametrize("kind", ["int64", "float32", "mixed"])
+def test_outermost_pass_width(hc, kind, cols, cols_outer):
+    """A separate width for the pass over the outermost axes: D = 14, c = 6
+    leaves 8 outer axes, two passes of 4; the second one takes cols_outer."""
+    D = 14
+    if kind == "int64":
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=cols + 100)
+        want = oracle.convolve(x, y, threads=8)
+    elif kind == "mixed":
+        x, y = inputs.uniform01_pair(D, seed=cols + 100)
+        want = oracle.convolve_mixed(x, y)
+    else:
+        x, y = inputs.normal_pair(D, seed=cols + 100, dtype=np.float32)
+        want = oracle.convolve(x, y, threads=8)
+    got = gpu_conv(hc, x, y, mixed=(kind == "mixed"), c=6, kmax=4, cols=cols, cols_outer=cols_outer)
+    assert_bit_equal(got, want)
+
+
 @pytest.mark.parametrize("cols", [-16, -32, 8])
 def test_chunked_outer_passes_tile_width(hc, cols):
     """The chunked schedule's whole-array passes (7 outer axes: 4 + 3) at a
