@@ -88,7 +88,30 @@ struct AdjSmem {
   static constexpr size_t bytes = kG + 2 * kLast + 2 * kH;
 };
 
+// Pipelined form (PIPE): the next tile's operand rows and G tile are copied
+// into shared memory with cp.async while the current tile is finished, so
+// that no stage waits on global loads.  Shared memory
+//   [Gs | LastX | LastY | Gpre | rows]:
+// the fused stage reads all its inputs (one pencil per thread) before any
+// thread writes, so Hs_x, Hs_y overwrite LastX, LastY, and the E^T group-1
+// output moves into Gs (dead after the fused stage).  The G tile is copied in
+// 16-byte pieces from the 16-byte boundary at or below its start and read
+// from its offset there.  The copies for tile t + grid are issued once tile
+// t has consumed its rows and its G tile (after I^T on group 0).
 template <class M, int C>
+struct AdjPipeSmem {
+  typedef AdjSmem<M, C> A;
+  static constexpr size_t kGs = (A::kG + 15) / 16 * 16;
+  static constexpr size_t kLastOff = kGs;
+  static constexpr size_t kPreOff = kLastOff + (2 * A::kLast + 15) / 16 * 16;
+  static constexpr size_t kPre = kGs + 16;
+  static constexpr size_t kRowsOff = kPreOff + kPre;
+  static constexpr size_t bytes = kRowsOff + 2 * sizeof(typename M::In) * (size_t)p2(C);
+  static_assert(A::kH <= A::kLast, "Hs overwrites the operand buffers");
+  static_assert(2 * A::kH1 <= A::kG, "E^T group-1 output fits in Gs");
+};
+
+template <class M, int C, bool PIPE>
 __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __restrict__ Gsrc,
                                                        const typename M::In* __restrict__ X,
                                                        const typename M::In* __restrict__ Y,
@@ -99,23 +122,57 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
   typedef typename M::W W;
   typedef AdjShape<C> S;
   typedef AdjSmem<M, C> SM;
+  typedef AdjPipeSmem<M, C> PS;
+  static_assert(!PIPE || S::G >= 2, "pipelined adjoint tiles: C >= 4");
   extern __shared__ __align__(16) unsigned char smem[];
   W* Gs = reinterpret_cast<W*>(smem);
   In* S1 = reinterpret_cast<In*>(smem);  // G == 3: aliases Gs (dead before Gs is written)
-  In* LastX = reinterpret_cast<In*>(smem + SM::kG);
-  In* LastY = reinterpret_cast<In*>(smem + SM::kG + SM::kLast);
-  W* HsX = reinterpret_cast<W*>(smem + SM::kG + 2 * SM::kLast);
-  W* HsY = reinterpret_cast<W*>(smem + SM::kG + 2 * SM::kLast + SM::kH);
-  W* H1X = reinterpret_cast<W*>(LastX);  // G == 3: E^T group-1 output
-  W* H1Y = reinterpret_cast<W*>(LastY);
+  In* LastX = reinterpret_cast<In*>(smem + (PIPE ? PS::kLastOff : SM::kG));
+  In* LastY = reinterpret_cast<In*>(smem + (PIPE ? PS::kLastOff : SM::kG) + SM::kLast);
+  W* HsX = PIPE ? reinterpret_cast<W*>(LastX) : reinterpret_cast<W*>(smem + SM::kG + 2 * SM::kLast);
+  W* HsY = PIPE ? reinterpret_cast<W*>(LastY)
+                : reinterpret_cast<W*>(smem + SM::kG + 2 * SM::kLast + SM::kH);
+  // G == 3: E^T group-1 output
+  W* H1X = PIPE ? Gs : reinterpret_cast<W*>(LastX);
+  W* H1Y = PIPE ? reinterpret_cast<W*>(smem + SM::kH1) : reinterpret_cast<W*>(LastY);
+  unsigned char* Gpre = smem + PS::kPreOff;
+  In* rows = reinterpret_cast<In*>(smem + PS::kRowsOff);  // [operand][2^C]
   const int tid = threadIdx.x, nt = blockDim.x;
   const bool want_x = Hx != nullptr, want_y = Hy != nullptr;
+  const char* gend = reinterpret_cast<const char*>(Gsrc + ntiles * p3(C));
+  auto prefetch = [&](long long t) {
+#pragma unroll 1
+    for (int e = tid; e < 2 * p2(C); e += nt) {
+      const int op = e >> C, i = e & (p2(C) - 1);
+      cp_async<sizeof(In)>(rows + op * p2(C) + i, (op ? Y : X) + t * p2(C) + i);
+    }
+    const char* ga = reinterpret_cast<const char*>(Gsrc + t * p3(C));
+    const unsigned mis = (unsigned)(reinterpret_cast<uintptr_t>(ga) & 15);
+    const char* g0 = ga - mis;
+    const int nch = (int)((mis + sizeof(W) * (size_t)p3(C) + 15) / 16);
+#pragma unroll 1
+    for (int c = tid; c < nch; c += nt) {
+      const char* src = g0 + 16 * (size_t)c;
+      const long long rem = gend - src;
+      cp_async16(Gpre + 16 * c, src, rem < 16 ? (int)rem : 16);
+    }
+    cp_async_commit();
+  };
+  if constexpr (PIPE) {
+    if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x);
+  }
 
 #pragma unroll 1
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const In* xr = X + t * p2(C);
-    const In* yr = Y + t * p2(C);
+    if constexpr (PIPE) {
+      cp_async_wait<0>();
+      __syncthreads();  // this tile's rows and G tile are in shared memory
+    }
+    const In* xr = PIPE ? rows : X + t * p2(C);
+    const In* yr = PIPE ? rows + p2(C) : Y + t * p2(C);
     const W* gr = Gsrc + t * p3(C);
+    if constexpr (PIPE)
+      gr = reinterpret_cast<const W*>(Gpre + (reinterpret_cast<uintptr_t>(gr) & 15));
     if constexpr (S::G == 1) {
       if (tid == 0) {
         W g[p3(C)];
@@ -201,6 +258,10 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
         }
       }
       __syncthreads();
+      if constexpr (PIPE) {
+        // rows and Gpre are consumed: start the copies of the next tile
+        if (t + gridDim.x < ntiles) prefetch(t + gridDim.x);
+      }
       // ---- I^T on group 1 (3 groups)
       if constexpr (S::G == 3) {
         constexpr int O = p3(S::g0), R = 27;
@@ -217,7 +278,50 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
         __syncthreads();
       }
       // ---- fused: I^T innermost group, products, E^T innermost group
-      {
+      if constexpr (PIPE) {
+        // one pencil per thread (NO <= blockDim.x); all reads, then all writes
+        constexpr int NO = S::NO;
+        const int o = tid;
+        W g[27];
+        In ay[8], ax[8];
+        if (o < NO) {
+#pragma unroll
+          for (int j = 0; j < 27; ++j) g[j] = Gs[o * 27 + j];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            ay[q] = LastY[q * NO + o];
+            ax[q] = LastX[q * NO + o];
+          }
+        }
+        __syncthreads();
+        if (o < NO) {
+          interp_t_pencil<M, 3>(g);
+          if (want_x) {
+            In a[27];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = ay[q];
+            eval_pencil<M, 3>(a);
+            W h[27];
+#pragma unroll
+            for (int j = 0; j < 27; ++j) h[j] = M::mulw(g[j], a[j]);
+            eval_t_pencil<M, 3>(h);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) HsX[b * NO + o] = h[b];
+          }
+          if (want_y) {
+            In a[27];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = ax[q];
+            eval_pencil<M, 3>(a);
+            W h[27];
+#pragma unroll
+            for (int j = 0; j < 27; ++j) h[j] = M::mulw(g[j], a[j]);
+            eval_t_pencil<M, 3>(h);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) HsY[b * NO + o] = h[b];
+          }
+        }
+      } else {
         constexpr int NO = S::NO;
 #pragma unroll 1
         for (int o = tid; o < NO; o += nt) {
@@ -439,16 +543,50 @@ static cudaError_t launch_et(int K, const typename M::W* sx, const typename M::W
   return cudaErrorInvalidValue;
 }
 
+constexpr int adj_threads(int C) { return C >= 6 ? 256 : (C >= 4 ? 128 : 32); }
+
+// The pipelined form where it keeps as many resident CTAs per SM as the
+// plain one (its extra shared memory and registers may cost occupancy).
+template <class M, int C>
+static bool use_pipe_adj() {
+  static int choice = -1;  // per instantiation; every thread computes the same value
+  if (choice < 0) {
+    int pipe = 0, plain = 0;
+    const int threads = adj_threads(C);
+    if (prep_kernel(tile_adj_kernel<M, C, true>, AdjPipeSmem<M, C>::bytes) != cudaSuccess ||
+        prep_kernel(tile_adj_kernel<M, C, false>, AdjSmem<M, C>::bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pipe, tile_adj_kernel<M, C, true>, threads,
+                                                      AdjPipeSmem<M, C>::bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&plain, tile_adj_kernel<M, C, false>, threads,
+                                                      AdjSmem<M, C>::bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    choice = pipe >= plain && pipe > 0 ? 1 : 0;
+  }
+  return choice == 1;
+}
+
 template <class M, int C>
 static cudaError_t launch_adj_c(const typename M::W* G, const typename M::In* X,
                                 const typename M::In* Y, typename M::W* Hx, typename M::W* Hy,
                                 long long ntiles, cudaStream_t st) {
-  const size_t smem = AdjSmem<M, C>::bytes;
-  auto k = tile_adj_kernel<M, C>;
   ProfileScope prof(st, "tile_adj");
+  const int threads = adj_threads(C);
+  if constexpr (AdjShape<C>::G >= 2) {
+    if ((reinterpret_cast<uintptr_t>(G) & 15) == 0 && use_pipe_adj<M, C>()) {
+      const size_t smem = AdjPipeSmem<M, C>::bytes;
+      auto k = tile_adj_kernel<M, C, true>;
+      cudaError_t e = prep_kernel(k, smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(G, X, Y, Hx, Hy, ntiles);
+      return cudaGetLastError();
+    }
+  }
+  const size_t smem = AdjSmem<M, C>::bytes;
+  auto k = tile_adj_kernel<M, C, false>;
   cudaError_t e = prep_kernel(k, smem);
   if (e != cudaSuccess) return e;
-  const int threads = C >= 6 ? 256 : (C >= 4 ? 128 : 32);
   k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(G, X, Y, Hx, Hy, ntiles);
   return cudaGetLastError();
 }

@@ -105,6 +105,37 @@ struct TileRows {
   static constexpr size_t bytes = kOff + 2 * 2 * sizeof(typename M::In) * (size_t)p2(C);
 };
 
+// Bulk (TMA engine) shared -> global store of `bytes` bytes; both addresses
+// 16-byte aligned, bytes a multiple of 16.  One thread issues it; the shared
+// source must have been fenced for the async proxy (fence.proxy.async).
+__device__ __forceinline__ void bulk_store(void* gmem, const void* smem, unsigned bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gmem), "r"(s),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// Wait until at most N of this thread's bulk groups are still reading their
+// shared source (READ) or still in flight at all.
+template <int N, bool READ>
+__device__ __forceinline__ void bulk_wait() {
+  if constexpr (READ)
+    asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+  else
+    asm volatile("cp.async.bulk.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared memory of the tile kernel that stores its tiles with bulk copies:
+// two W tiles (tile t computes in buffer t & 1 while the copy of tile t - 1
+// drains the other), each with 16 spare bytes so the tile can be placed at
+// its output's address modulo 16, then the [buffer][operand][2^C] rows.
+template <class M, int C>
+struct TileBulk {
+  static constexpr size_t kWB = (TileSmem<M, C>::bytes + 15) / 16 * 16 + 16;
+  static constexpr size_t kOff = 2 * kWB;
+  static constexpr size_t bytes = kOff + 2 * 2 * sizeof(typename M::In) * (size_t)p2(C);
+};
+
 // Loader: ld(op, i) returns element i of the tile's operand row (op 0 = x,
 // 1 = y), already evaluated on the outer axes.  out_tile: the tile's 3^C
 // outputs.  smem: TileSmem<M, C>::bytes of shared memory.
@@ -135,7 +166,11 @@ inline size_t tile_smem_bytes(hc_dtype dt, int C) {
   return 0;
 }
 
-template <class M, int C, bool FINAL, class Loader>
+// SMEM_OUT (intermediate tiles only, FINAL false): the last stage writes the
+// finished tile back into the W tile in shared memory (in place, each thread
+// its own pencils; out_tile unused) and fences it for the async proxy, so
+// that the caller can store it with one bulk copy.
+template <class M, int C, bool FINAL, class Loader, bool SMEM_OUT = false>
 __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ out_tile,
                                           unsigned char* smem) {
   typedef typename M::In In;
@@ -290,7 +325,10 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
 #pragma unroll
           for (int j = 0; j < p3(S::g0); ++j) v[j] = Ws[j * R + r];
           interp_pencil<M, S::g0>(v);
-          if constexpr (FINAL) {
+          if constexpr (SMEM_OUT) {
+#pragma unroll
+            for (int j = 0; j < p3(S::g0); ++j) Ws[j * R + r] = v[j];
+          } else if constexpr (FINAL) {
             Out* o = reinterpret_cast<Out*>(out_tile);
 #pragma unroll
             for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = M::out(v[j]);
@@ -300,6 +338,10 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
             for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = v[j];
           }
         }
+      }
+      if constexpr (SMEM_OUT) {
+        static_assert(!FINAL, "bulk tile stores write the intermediate W");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       }
       __syncthreads();  // the caller's next tile reuses shared memory
     }
