@@ -73,6 +73,8 @@ def _peaks():
 # counting a fused multiply-add as two): 0.625e12 FP64 add, subtract or
 # multiply instructions per second.
 FP64_OPS_PEAK = 0.625e12
+L2_BYTES = 129 << 20  # GB300 L2 (rounded up)
+L2_FLUSH_BYTES = 256 << 20
 
 
 def _src_hash():
@@ -214,7 +216,7 @@ class Workload:
             self.dtype = "f32"
             self.D = None
         elif name == "fwdbwd":
-            D = 18
+            D = D_override or 18
             self.D = D
             x = inputs.normal(1 << D, seed, np.float32)
             y = inputs.normal(1 << D, seed + 1, np.float32)
@@ -388,9 +390,16 @@ def _time_steps(wl, steps, warmup, dist):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     graph_events = []
+    # A working set below L2 would stay resident from one step to the next:
+    # flush L2 between steps (outside the per-step events) and time the steps
+    # by their own events.
+    flush = (torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=wl.dev)
+             if wl.alg_bytes < L2_BYTES else None)
     e0.record(stream)
     for _ in range(steps):
-        if wl.name == "batched" or wl.graph is not None:
+        if flush is not None:
+            flush.fill_(1)
+        if wl.name == "batched" or wl.graph is not None or flush is not None:
             # the tracer does not see inside graph replays, so time each replay
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -403,10 +412,12 @@ def _time_steps(wl, steps, warmup, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    if flush is not None:
+        ms = sum(a.elapsed_time(b) for a, b in graph_events)
     _lib.lib().hc_profile_enable(0)
     clk = clocks.stop()
     prof = _lib.profile_collect()
-    if graph_events:
+    if graph_events and (wl.name == "batched" or wl.graph is not None):
         # The tracer does not see inside graph replays: the per-kernel split
         # comes from one eager launch of the same batch after the timed
         # region, scaled to the timed steps (the step time itself is the
@@ -678,7 +689,7 @@ def main():
                     help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked) "
                          "instead of the tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
-    if args.D is not None and args.workload not in SINGLE:
+    if args.D is not None and args.workload not in SINGLE + ("fwdbwd",):
         ap.error("--D applies to single-instance workloads only")
     if args.steps is None:
         args.steps = DEFAULT_STEPS[args.workload]
@@ -762,8 +773,9 @@ def main():
                                        "timed graph replays, scaled by steps"}
                       if args.workload == "batched" or wl.graph is not None else {}),
                    "l2": "working set larger than L2 (129 MB); no flush"
-                   if args.workload in ("d20_int64", "d16_fp64", "d16_mixed", "batched", "fwdbwd")
-                   else "L2 flushed: no (working set below L2)"},
+                   if wl.alg_bytes >= L2_BYTES else
+                   "working set below L2: L2 flushed between steps (256 MB write, "
+                   "outside the per-step CUDA events; time = sum of the steps' events)"},
         "roofline": roof,
         "alg_hbm_frac": (wl.alg_bytes * args.steps / (ms / 1e3) / 1e9) / peak_hbm,
         "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()},

@@ -79,10 +79,17 @@ struct AdjSmem {
   typedef typename M::W W;
   typedef AdjShape<C> S;
   static constexpr size_t kG = sizeof(W) * (size_t)p3(C);
-  static constexpr size_t kLast = sizeof(In) * (size_t)p2(S::gL) * S::NO;  // per operand
-  static constexpr size_t kH = sizeof(W) * (size_t)p2(S::gL) * S::NO;      // per operand
-  static constexpr size_t kS1 = S::G == 3 ? 2 * sizeof(In) * (size_t)p3(S::g0) * p2(C - S::g0) : 0;
-  static constexpr size_t kH1 = S::G == 3 ? sizeof(W) * (size_t)p3(S::g0) * 64 : 0;  // per operand
+  // Row strides chosen against shared-memory bank conflicts: LP for the
+  // transposed [2^gL][LP] operand and product buffers (stage-1 writes, E^T
+  // group-1 reads), S1R for the stage-0 output rows (stage-1 reads), H1R for
+  // the E^T group-1 output rows (its writes).
+  static constexpr int LP = S::G == 3 ? padded_rows(S::NO, (int)sizeof(In)) : S::NO;
+  static constexpr int S1R = p2(C - S::g0) + (p2(C - S::g0) % 16 == 0 ? 8 : 0);
+  static constexpr int H1R = 72;
+  static constexpr size_t kLast = sizeof(In) * (size_t)p2(S::gL) * LP;  // per operand
+  static constexpr size_t kH = sizeof(W) * (size_t)p2(S::gL) * LP;      // per operand
+  static constexpr size_t kS1 = S::G == 3 ? 2 * sizeof(In) * (size_t)p3(S::g0) * S1R : 0;
+  static constexpr size_t kH1 = S::G == 3 ? sizeof(W) * (size_t)p3(S::g0) * H1R : 0;  // per operand
   static_assert(kS1 <= kG, "stage-0 buffer fits in the G tile");
   static_assert(kH1 <= kLast, "E^T group-1 output fits in the operand buffer");
   static constexpr size_t bytes = kG + 2 * kLast + 2 * kH;
@@ -218,9 +225,9 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
 #pragma unroll
             for (int j = 0; j < p3(S::g0); ++j) d[r * p3(S::g0) + j] = v[j];
           } else {
-            In* d = S1 + op * (p3(S::g0) * R);
+            In* d = S1 + op * (p3(S::g0) * SM::S1R);
 #pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) d[j * R + r] = v[j];
+            for (int j = 0; j < p3(S::g0); ++j) d[j * SM::S1R + r] = v[j];
           }
         }
       }
@@ -233,14 +240,14 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
         for (int p = tid; p < 2 * NP; p += nt) {
           const int op = p / NP, q = p - op * NP;
           const int o = q / R, r = q - o * R;
-          const In* s = S1 + op * (O * 8 * R);
+          const In* s = S1 + op * (O * SM::S1R);
           In v[27];
 #pragma unroll
-          for (int b = 0; b < 8; ++b) v[b] = s[(o * 8 + b) * R + r];
+          for (int b = 0; b < 8; ++b) v[b] = s[o * SM::S1R + b * R + r];
           eval_pencil<M, 3>(v);
           In* d = op ? LastY : LastX;
 #pragma unroll
-          for (int j = 0; j < 27; ++j) d[r * (O * 27) + o * 27 + j] = v[j];
+          for (int j = 0; j < 27; ++j) d[r * SM::LP + o * 27 + j] = v[j];
         }
         __syncthreads();
       }
@@ -264,10 +271,12 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
       }
       // ---- I^T on group 1 (3 groups)
       if constexpr (S::G == 3) {
+        // the group-0 digit o runs fastest across threads (no bank overlap
+        // between two 27-element runs within a warp)
         constexpr int O = p3(S::g0), R = 27;
 #pragma unroll 1
         for (int p = tid; p < O * R; p += nt) {
-          const int o = p / R, r = p - o * R;
+          const int r = p / O, o = p - r * O;
           W v[27];
 #pragma unroll
           for (int j = 0; j < 27; ++j) v[j] = Gs[(o * 27 + j) * R + r];
@@ -289,8 +298,8 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
           for (int j = 0; j < 27; ++j) g[j] = Gs[o * 27 + j];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            ay[q] = LastY[q * NO + o];
-            ax[q] = LastX[q * NO + o];
+            ay[q] = LastY[q * SM::LP + o];
+            ax[q] = LastX[q * SM::LP + o];
           }
         }
         __syncthreads();
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
             for (int j = 0; j < 27; ++j) h[j] = M::mulw(g[j], a[j]);
             eval_t_pencil<M, 3>(h);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) HsX[b * NO + o] = h[b];
+            for (int b = 0; b < 8; ++b) HsX[b * SM::LP + o] = h[b];
           }
           if (want_y) {
             In a[27];
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
             for (int j = 0; j < 27; ++j) h[j] = M::mulw(g[j], a[j]);
             eval_t_pencil<M, 3>(h);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) HsY[b * NO + o] = h[b];
+            for (int b = 0; b < 8; ++b) HsY[b * SM::LP + o] = h[b];
           }
         }
       } else {
@@ -332,25 +341,25 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
           In a[27];
           if (want_x) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = LastY[q * NO + o];
+            for (int q = 0; q < 8; ++q) a[q] = LastY[q * SM::LP + o];
             eval_pencil<M, 3>(a);
             W h[27];
 #pragma unroll
             for (int j = 0; j < 27; ++j) h[j] = M::mulw(g[j], a[j]);
             eval_t_pencil<M, 3>(h);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) HsX[b * NO + o] = h[b];
+            for (int b = 0; b < 8; ++b) HsX[b * SM::LP + o] = h[b];
           }
           if (want_y) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = LastX[q * NO + o];
+            for (int q = 0; q < 8; ++q) a[q] = LastX[q * SM::LP + o];
             eval_pencil<M, 3>(a);
             W h[27];
 #pragma unroll
             for (int j = 0; j < 27; ++j) h[j] = M::mulw(g[j], a[j]);
             eval_t_pencil<M, 3>(h);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) HsY[b * NO + o] = h[b];
+            for (int b = 0; b < 8; ++b) HsY[b * SM::LP + o] = h[b];
           }
         }
       }
@@ -367,11 +376,11 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
           const W* s = op ? HsY : HsX;
           W v[27];
 #pragma unroll
-          for (int j = 0; j < 27; ++j) v[j] = s[b2 * NO + o * 27 + j];
+          for (int j = 0; j < 27; ++j) v[j] = s[b2 * SM::LP + o * 27 + j];
           eval_t_pencil<M, 3>(v);
           W* d = op ? H1Y : H1X;
 #pragma unroll
-          for (int b1 = 0; b1 < 8; ++b1) d[(o * 8 + b1) * 8 + b2] = v[b1];
+          for (int b1 = 0; b1 < 8; ++b1) d[o * SM::H1R + b1 * 8 + b2] = v[b1];
         }
         __syncthreads();
         // ---- E^T on group 0 -> global, element (b0, b1, b2) at b0 * 64 + b1 * 8 + b2
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(256) tile_adj_kernel(const typename M::W* __re
           const W* s = op ? H1Y : H1X;
           W v[p3(S::g0)];
 #pragma unroll
-          for (int j = 0; j < p3(S::g0); ++j) v[j] = s[j * R + r];
+          for (int j = 0; j < p3(S::g0); ++j) v[j] = s[j * SM::H1R + r];
           eval_t_pencil<M, S::g0>(v);
           W* d = (op ? Hy : Hx) + t * p2(C);
 #pragma unroll

@@ -66,14 +66,24 @@ struct TileShape {
   static constexpr int nLastPencils = p3(C - gL);     // pencils of the fused stage
 };
 
+// Row stride (elements) of a transposed [2^gL][n] buffer written by stage 1:
+// the smallest stride >= n whose byte size is 16 modulo 32, so that the
+// stage's writes (8 consecutive lanes on 8 rows) fall in distinct banks.
+constexpr int padded_rows(int n, int elem_bytes) {
+  return (n * elem_bytes) % 32 == 16 ? n : padded_rows(n + 1, elem_bytes);
+}
+
 template <class M, int C>
 struct TileSmem {
   typedef typename M::In In;
   typedef typename M::W W;
   // W tile; the stage-0 buffer of a 3-group tile lives inside it.
   static constexpr size_t kW = sizeof(W) * (size_t)p3(C);
-  // transposed buffer feeding the fused stage, per operand
-  static constexpr size_t kLast = sizeof(In) * (size_t)p2(TileShape<C>::gL) * p3(C - TileShape<C>::gL);
+  // transposed buffer feeding the fused stage, per operand: [2^gL][LP]
+  static constexpr int LP = TileShape<C>::G == 3
+                                ? padded_rows(TileShape<C>::nLastPencils, (int)sizeof(In))
+                                : TileShape<C>::nLastPencils;
+  static constexpr size_t kLast = sizeof(In) * (size_t)p2(TileShape<C>::gL) * LP;
   // stage-0 output [operand][3^g0][S1R]: rows padded so that the stage-1
   // reads of two neighbouring rows fall in different banks
   static constexpr int S1R = p2(C - TileShape<C>::g0) + (p2(C - TileShape<C>::g0) % 16 == 0 ? 8 : 0);
@@ -178,8 +188,9 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
   typedef typename M::Out Out;
   typedef TileShape<C> S;
   W* Ws = reinterpret_cast<W*>(smem);
+  constexpr int LP = TileSmem<M, C>::LP;  // row stride of LastX, LastY
   In* LastX = reinterpret_cast<In*>(smem + TileSmem<M, C>::kLastOff);
-  In* LastY = LastX + p2(S::gL) * p3(C - S::gL);
+  In* LastY = LastX + p2(S::gL) * LP;
   In* S1 = reinterpret_cast<In*>(smem);  // G == 3 only; aliases the W tile
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
@@ -252,7 +263,7 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
           eval_pencil<M, 3>(v);
           In* d = op ? LastY : LastX;
 #pragma unroll
-          for (int j = 0; j < 27; ++j) d[r * (O * 27) + o * 27 + j] = v[j];
+          for (int j = 0; j < 27; ++j) d[r * LP + o * 27 + j] = v[j];
         }
         __syncthreads();
       }
@@ -265,8 +276,8 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
         if (o < NO) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            a[q] = LastX[q * NO + o];
-            b[q] = LastY[q * NO + o];
+            a[q] = LastX[q * LP + o];
+            b[q] = LastY[q * LP + o];
           }
         }
         __syncthreads();
@@ -287,8 +298,8 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
           In a[27], b[27];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            a[q] = LastX[q * NO + o];
-            b[q] = LastY[q * NO + o];
+            a[q] = LastX[q * LP + o];
+            b[q] = LastY[q * LP + o];
           }
           eval_pencil<M, 3>(a);
           eval_pencil<M, 3>(b);
@@ -301,12 +312,14 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
         }
       }
       __syncthreads();
-      // ---- interpolate group 1 (G == 3) in shared memory.
+      // ---- interpolate group 1 (G == 3) in shared memory.  The group-0
+      // digit o runs fastest across threads: lanes then never straddle two
+      // 27-element runs of one o, whose banks would overlap.
       if constexpr (S::G == 3) {
         constexpr int O = p3(S::g0), R = 27;
         #pragma unroll 1
         for (int p = tid; p < O * R; p += nt) {
-          const int o = p / R, r = p - o * R;
+          const int r = p / O, o = p - r * O;
           W v[27];
 #pragma unroll
           for (int j = 0; j < 27; ++j) v[j] = Ws[(o * 27 + j) * R + r];

@@ -378,6 +378,62 @@ def test_convolve_out_device_arrays_and_argument_checks(hc):
     torch.cuda.synchronize()
 
 
+def _cudart():
+    import ctypes
+    import glob
+    import os
+    cands = [os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcudart.so")]
+    cands += sorted(glob.glob("/usr/local/cuda*/lib64/libcudart.so*"))
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    pytest.skip("no shared CUDA runtime to allocate managed memory with")
+
+
+@pytest.mark.parametrize("kind", ["int64", "float32"])
+def test_managed_output_takes_per_thread_tile_stores(hc, kind):
+    """Intermediate tiles go out with bulk (TMA engine) copies only into plain
+    device allocations; a managed z takes the per-thread stores.  Both give
+    the oracle's bits."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib
+    rt = _cudart()
+    D = 12
+    if kind == "int64":
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=41)
+        code, es, dt = _lib.HC_INT64, 8, np.int64
+    else:
+        x, y = inputs.normal_pair(D, seed=41, dtype=np.float32)
+        code, es, dt = _lib.HC_FP32, 4, np.float32
+    want = oracle.convolve(x, y)
+    lib = _lib.lib()
+    s = _lib.hc_schedule(1, 8, 4, 16, 0)
+    nb = int(lib.hc_workspace_size_schedule(D, code, ctypes.byref(s)))
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=DEV)
+    xd, yd = T(x), T(y)
+    ptr = ctypes.c_void_p()
+    assert rt.cudaMallocManaged(ctypes.byref(ptr), ctypes.c_size_t(es * 3 ** D), 1) == 0
+    try:
+        st = torch.cuda.current_stream().cuda_stream
+        assert lib.hc_convolve_schedule(xd.data_ptr(), yd.data_ptr(), ptr.value, D, code,
+                                        ctypes.byref(s), ws.data_ptr(), nb, st) == 0
+        torch.cuda.synchronize()
+        got = np.ctypeslib.as_array((ctypes.c_byte * (es * 3 ** D)).from_address(ptr.value))
+        assert_bit_equal(got.view(dt).copy(), want)
+        zd = torch.empty(3 ** D, dtype=torch.int64 if kind == "int64" else torch.float32,
+                         device=DEV)
+        assert lib.hc_convolve_schedule(xd.data_ptr(), yd.data_ptr(), zd.data_ptr(), D, code,
+                                        ctypes.byref(s), ws.data_ptr(), nb, st) == 0
+        torch.cuda.synchronize()
+        assert_bit_equal(zd.cpu().numpy(), want)
+    finally:
+        torch.cuda.synchronize()
+        rt.cudaFree(ptr)
+
+
 def test_shaped_input_gives_shaped_output(hc):
     x = torch.arange(1, 9, dtype=torch.float64, device=DEV).reshape(2, 2, 2)
     z = hc.convolve(x, x)
