@@ -499,6 +499,21 @@ def _comparisons(wl, ms_per_step):
     return None
 
 
+def _timed_host_steps(one, min_steps, warmup, min_seconds=1.0, max_steps=100):
+    """Host wall-clock time of repeated synchronous end-to-end steps: at least
+    min_steps and about min_seconds (one untimed step sizes the count)."""
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    one()
+    t1 = time.perf_counter() - t0
+    steps = max(min_steps, min(max_steps, int(min_seconds / max(t1, 1e-6)) + 1))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    return steps, time.perf_counter() - t0
+
+
 def _e2e(wl, steps=3, warmup=1):
     """Same metric through the public API with host (pinned) buffers: every
     step copies x, y to the device, convolves, and copies z back."""
@@ -514,13 +529,11 @@ def _e2e(wl, steps=3, warmup=1):
     # the device-resident output is not needed here
     wl.z = None
     torch.cuda.empty_cache()
-    for _ in range(warmup):
+    def one():
         hc.convolve(xh, yh, out=zh, mixed=wl.mixed, workspace=wl.ws)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        hc.convolve(xh, yh, out=zh, mixed=wl.mixed, workspace=wl.ws)
-    dt = time.perf_counter() - t0
-    return {"value": wl.outputs * steps / dt, "unit": UNIT,
+
+    steps, dt = _timed_host_steps(one, steps, warmup)
+    return {"value": wl.outputs * steps / dt, "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": int(2 * x.nbytes), "d2h_bytes_per_step": int(zh.numel() * zh.element_size())}
 
 
@@ -560,13 +573,8 @@ def _e2e_other(wl, steps, warmup):
             gxh.copy_(xd.grad, non_blocking=True)
             gyh.copy_(yd.grad, non_blocking=True)
             loss.item()
-    for _ in range(warmup):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
-    dt = time.perf_counter() - t0
-    return {"value": wl.outputs * steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    steps, dt = _timed_host_steps(one, steps, warmup)
+    return {"value": wl.outputs * steps / dt, "unit": UNIT, "steps": steps, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
 
 
