@@ -121,6 +121,26 @@ __global__ void __launch_bounds__(256) group_tile_kernel(const GroupPtrs* __rest
   }
 }
 
+// The same group tiles (intermediate only) stored with bulk copies
+// (tile_loop_bulk), when every instance's intermediate array of the group is
+// a plain device allocation.
+template <class M, int C>
+__global__ void __launch_bounds__(256) group_tile_bulk_kernel(const GroupPtrs* __restrict__ tab,
+                                                              const typename M::In* __restrict__ X,
+                                                              const typename M::In* __restrict__ Y,
+                                                              long long per, long long ntiles) {
+  typedef typename M::In In;
+  typedef typename M::W W;
+  extern __shared__ __align__(16) unsigned char smem[];
+  tile_loop_bulk<M, C>(
+      [&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); },
+      [&](long long t) {
+        const long long i = t / per, local = t - i * per;
+        return reinterpret_cast<W*>(tab[i].w) + local * p3(C);
+      },
+      ntiles, smem);
+}
+
 // Interpolation of the a = K1 + K2 outer axes of every instance of a group,
 // in place on its [3^a][lo] intermediate (FINAL: written to its output in
 // the output type).  Tile t: instance t / per, columns (t % per) * L ...;
@@ -168,6 +188,7 @@ __global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256)
 // One group of the grouped form: the instances with one D.
 struct GroupPlan {
   int D, C, a, n;
+  bool bulk = false;  // every intermediate array is a plain device allocation
   size_t off_tab;           // GroupPtrs[n]
   size_t off_xo, off_yo;    // operands evaluated on the a outer axes, [n][3^a][2^C]
   size_t off_tx, off_ty;    // first evaluation pass when a > 3, [n][3^3][2^(D-3)]
@@ -363,10 +384,20 @@ static cudaError_t launch_group_eval_k(const GroupPtrs* tab, int n, long long lo
 template <class M, int C, bool FINAL>
 static cudaError_t launch_group_tile_c(const GroupPtrs* tab, const typename M::In* X,
                                        const typename M::In* Y, long long per, long long ntiles,
-                                       cudaStream_t st) {
+                                       bool bulk, cudaStream_t st) {
+  ProfileScope prof(st, "batched_tile");
+  if constexpr (use_bulk_tiles<M, C, FINAL>()) {
+    if (bulk) {
+      const size_t smem = TileBulk<M, C>::bytes;
+      auto k = group_tile_bulk_kernel<M, C>;
+      cudaError_t e = prep_kernel(k, smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid_for(k, 256, smem, ntiles), 256, smem, st>>>(tab, X, Y, per, ntiles);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = TileRows<M, C>::bytes;
   auto k = group_tile_kernel<M, C, FINAL>;
-  ProfileScope prof(st, "batched_tile");
   cudaError_t e = prep_kernel(k, smem);
   if (e != cudaSuccess) return e;
   const int threads = C >= 4 ? 256 : 32;
@@ -377,19 +408,19 @@ static cudaError_t launch_group_tile_c(const GroupPtrs* tab, const typename M::I
 template <class M, bool FINAL>
 static cudaError_t launch_group_tile(int C, const GroupPtrs* tab, const typename M::In* X,
                                      const typename M::In* Y, long long per, long long ntiles,
-                                     cudaStream_t st) {
+                                     bool bulk, cudaStream_t st) {
   switch (C) {
-    case 1: return launch_group_tile_c<M, 1, FINAL>(tab, X, Y, per, ntiles, st);
-    case 2: return launch_group_tile_c<M, 2, FINAL>(tab, X, Y, per, ntiles, st);
-    case 3: return launch_group_tile_c<M, 3, FINAL>(tab, X, Y, per, ntiles, st);
-    case 4: return launch_group_tile_c<M, 4, FINAL>(tab, X, Y, per, ntiles, st);
-    case 5: return launch_group_tile_c<M, 5, FINAL>(tab, X, Y, per, ntiles, st);
-    case 6: return launch_group_tile_c<M, 6, FINAL>(tab, X, Y, per, ntiles, st);
-    case 7: return launch_group_tile_c<M, 7, FINAL>(tab, X, Y, per, ntiles, st);
-    case 8: return launch_group_tile_c<M, 8, FINAL>(tab, X, Y, per, ntiles, st);
+    case 1: return launch_group_tile_c<M, 1, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 2: return launch_group_tile_c<M, 2, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 3: return launch_group_tile_c<M, 3, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 4: return launch_group_tile_c<M, 4, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 5: return launch_group_tile_c<M, 5, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 6: return launch_group_tile_c<M, 6, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 7: return launch_group_tile_c<M, 7, FINAL>(tab, X, Y, per, ntiles, bulk, st);
+    case 8: return launch_group_tile_c<M, 8, FINAL>(tab, X, Y, per, ntiles, bulk, st);
     case 9:
       if constexpr (sizeof(typename M::W) == 4)
-        return launch_group_tile_c<M, 9, FINAL>(tab, X, Y, per, ntiles, st);
+        return launch_group_tile_c<M, 9, FINAL>(tab, X, Y, per, ntiles, bulk, st);
       return cudaErrorInvalidValue;
   }
   return cudaErrorInvalidValue;
@@ -459,9 +490,9 @@ static cudaError_t launch_groups_m(const BatchPlan& p, unsigned char* ws, cudaSt
     }
     const long long per = (long long)pow3z(g.a), ntiles = (long long)g.n * per;
     if (g.a == 0)
-      e = launch_group_tile<M, true>(g.C, tab, nullptr, nullptr, 1, ntiles, st);
+      e = launch_group_tile<M, true>(g.C, tab, nullptr, nullptr, 1, ntiles, false, st);
     else
-      e = launch_group_tile<M, false>(g.C, tab, X, Y, per, ntiles, st);
+      e = launch_group_tile<M, false>(g.C, tab, X, Y, per, ntiles, g.bulk, st);
     if (e != cudaSuccess) return e;
     if (g.a > 0) {
       e = launch_group_interp<M, kMixed>(g.a, tab, g.n, (long long)pow3z(g.C), st);
@@ -518,6 +549,13 @@ static hc_status prepare(const hc_instance* inst, int n, hc_dtype dtype, int fus
   std::vector<std::vector<GroupPtrs>> gtabs;
   s = build_batch(inst, n, dtype, fused_max_d, &p, &descs, &table, &gtabs, workspace);
   if (s != HC_OK) return s;
+  // groups whose intermediate arrays are all plain device allocations store
+  // their tiles with bulk copies (checked once here, not at every launch)
+  for (size_t g = 0; g < p.groups.size(); ++g) {
+    bool all = p.groups[g].a > 0;
+    for (size_t k = 0; all && k < gtabs[g].size(); ++k) all = is_device_allocation(gtabs[g][k].w);
+    p.groups[g].bulk = all;
+  }
   unsigned char* ws = (unsigned char*)workspace;
   cudaError_t e = cudaSuccess;
   if (p.n > 0)

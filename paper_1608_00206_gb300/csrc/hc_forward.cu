@@ -64,62 +64,17 @@ __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __
   }
 }
 
-// K2 with bulk stores: the same tiles, but each finished tile is written
-// back into shared memory and stored by the TMA engine with one bulk copy,
-// which drains while the CTA computes the next tile in the other W buffer
-// (the per-thread stores of the last stage otherwise bunch up the tile's
-// whole output at its end).  The W buffer is placed at the output's address
-// modulo 16, so that shared and global addresses agree in their low bits;
-// the elements before the output's first 16-byte boundary and after its
-// last are stored by threads.
+// K2 with bulk stores (tile_loop_bulk): intermediate tiles into a plain
+// device allocation.
 template <class M, int C>
 __global__ void __launch_bounds__(256) tile_conv_bulk_kernel(const typename M::In* __restrict__ X,
                                                              const typename M::In* __restrict__ Y,
                                                              typename M::W* __restrict__ out,
                                                              long long ntiles) {
   typedef typename M::In In;
-  typedef typename M::W W;
-  static_assert(TileShape<C>::G >= 2, "bulk tiles: C >= 4");
-  typedef TileBulk<M, C> B;
-  constexpr int N = p3(C);
   extern __shared__ __align__(16) unsigned char smem[];
-  In* rows = reinterpret_cast<In*>(smem + B::kOff);  // [buffer][operand][2^C]
-  auto prefetch = [&](long long t, int b) {
-#pragma unroll 1
-    for (int e = threadIdx.x; e < 2 * p2(C); e += blockDim.x) {
-      const int op = e >> C, i = e & (p2(C) - 1);
-      cp_async<sizeof(In)>(rows + (b * 2 + op) * p2(C) + i, (op ? Y : X) + t * p2(C) + i);
-    }
-    cp_async_commit();
-  };
-  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0);
-  int it = 0;
-#pragma unroll 1
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it ^= 1) {
-    if (t + gridDim.x < ntiles) {
-      prefetch(t + gridDim.x, it ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    // the copy issued from buffer `it` two tiles ago has read its source
-    if (threadIdx.x == 0) bulk_wait<1, true>();
-    __syncthreads();  // this tile's rows are in buffer `it`; W buffer `it` is free
-    W* out_tile = out + t * N;
-    const unsigned mis = (unsigned)(reinterpret_cast<uintptr_t>(out_tile) & 15);
-    unsigned char* wb = smem + it * B::kWB + mis;
-    RowLoader<In> ld{rows + (it * 2 + 0) * p2(C), rows + (it * 2 + 1) * p2(C)};
-    tile_body<M, C, false, RowLoader<In>, true>(ld, nullptr, wb);
-    // the tile is in wb[0, N), fenced; head / body / tail split at 16-byte boundaries
-    const int head = mis ? (int)((16 - mis) / sizeof(W)) : 0;
-    const int body = (int)(((N - head) * sizeof(W)) / 16 * 16 / sizeof(W));
-    const W* ws = reinterpret_cast<const W*>(wb);
-    if (threadIdx.x == 0 && body > 0)
-      bulk_store(out_tile + head, ws + head, (unsigned)(body * sizeof(W)));
-    for (int e = threadIdx.x; e < head; e += blockDim.x) out_tile[e] = ws[e];
-    for (int e = head + body + threadIdx.x; e < N; e += blockDim.x) out_tile[e] = ws[e];
-  }
-  if (threadIdx.x == 0) bulk_wait<0, false>();
+  tile_loop_bulk<M, C>([&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); },
+                       [&](long long t) { return out + t * p3(C); }, ntiles, smem);
 }
 
 // D = 0: z[0] = x[0] * y[0].
@@ -138,25 +93,6 @@ static int max_tile_axes() {
 }
 
 static int threads_for_tile(int C) { return C >= 4 ? 256 : 32; }
-
-// Bulk tile stores where they apply: intermediate tiles (a final-tile
-// launch is a single tile, D <= C), C >= 4, and two CTAs with two W buffers
-// each still fit one SM's shared memory.
-template <class M, int C, bool FINAL>
-constexpr bool use_bulk_tiles() {
-  return !FINAL && C >= 4 && 2 * (TileBulk<M, C>::bytes + 1024) <= 228 * 1024;
-}
-
-// Bulk copies are issued only into plain device allocations (not managed or
-// host-mapped memory, which the per-thread stores handle).
-static bool is_device_allocation(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice;
-}
 
 template <class M, int C, bool FINAL>
 static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* Y, void* out,

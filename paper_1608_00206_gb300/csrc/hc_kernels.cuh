@@ -56,6 +56,25 @@ inline int grid_for(K kernel, int threads, size_t smem, long long work_items) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// Bulk tile stores where they apply: intermediate tiles (a final-tile
+// launch is a single tile, D <= C), C >= 4, and two CTAs with two W buffers
+// each still fit one SM's shared memory.
+template <class M, int C, bool FINAL>
+constexpr bool use_bulk_tiles() {
+  return !FINAL && C >= 4 && 2 * (TileBulk<M, C>::bytes + 1024) <= 228 * 1024;
+}
+
+// Bulk copies are issued only into plain device allocations (not managed or
+// host-mapped memory, which the per-thread stores handle).
+inline bool is_device_allocation(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
 template <class M, int K>
 inline cudaError_t launch_eval_k(const typename M::In* sx, const typename M::In* sy,
                                  typename M::In* dx, typename M::In* dy, long long hi, long long lo,

@@ -361,6 +361,65 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
   }
 }
 
+// Tile loop whose intermediate tiles are stored with bulk copies: each
+// finished tile is written back into shared memory and stored by the TMA
+// engine with one bulk copy, which drains while the CTA computes the next
+// tile in the other W buffer (the per-thread stores of the last stage
+// otherwise bunch up the tile's whole output at its end).  The W buffer is
+// placed at the output's address modulo 16, so that shared and global
+// addresses agree in their low bits; the elements before the output's first
+// 16-byte boundary and after its last are stored by threads.  The next
+// tile's rows are prefetched with cp.async.  src(t, op): tile t's operand row
+// (op 0 = x, 1 = y), 2^C elements; out(t): tile t's 3^C outputs, in a plain
+// device allocation.  smem: TileBulk<M, C>::bytes.  Tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...
+template <class M, int C, class SrcFn, class OutFn>
+__device__ __forceinline__ void tile_loop_bulk(SrcFn src, OutFn out, long long ntiles,
+                                               unsigned char* smem) {
+  typedef typename M::In In;
+  typedef typename M::W W;
+  static_assert(TileShape<C>::G >= 2, "bulk tiles: C >= 4");
+  typedef TileBulk<M, C> B;
+  constexpr int N = p3(C);
+  In* rows = reinterpret_cast<In*>(smem + B::kOff);  // [buffer][operand][2^C]
+  auto prefetch = [&](long long t, int b) {
+#pragma unroll 1
+    for (int e = threadIdx.x; e < 2 * p2(C); e += blockDim.x) {
+      const int op = e >> C, i = e & (p2(C) - 1);
+      cp_async<sizeof(In)>(rows + (b * 2 + op) * p2(C) + i, src(t, op) + i);
+    }
+    cp_async_commit();
+  };
+  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0);
+  int it = 0;
+#pragma unroll 1
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it ^= 1) {
+    if (t + gridDim.x < ntiles) {
+      prefetch(t + gridDim.x, it ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    // the copy issued from buffer `it` two tiles ago has read its source
+    if (threadIdx.x == 0) bulk_wait<1, true>();
+    __syncthreads();  // this tile's rows are in buffer `it`; W buffer `it` is free
+    W* out_tile = out(t);
+    const unsigned mis = (unsigned)(reinterpret_cast<uintptr_t>(out_tile) & 15);
+    unsigned char* wb = smem + it * B::kWB + mis;
+    RowLoader<In> ld{rows + (it * 2 + 0) * p2(C), rows + (it * 2 + 1) * p2(C)};
+    tile_body<M, C, false, RowLoader<In>, true>(ld, nullptr, wb);
+    // the tile is in wb[0, N), fenced; head / body / tail split at 16-byte boundaries
+    const int head = mis ? (int)((16 - mis) / sizeof(W)) : 0;
+    const int body = (int)(((N - head) * sizeof(W)) / 16 * 16 / sizeof(W));
+    const W* ws = reinterpret_cast<const W*>(wb);
+    if (threadIdx.x == 0 && body > 0)
+      bulk_store(out_tile + head, ws + head, (unsigned)(body * sizeof(W)));
+    for (int e = threadIdx.x; e < head; e += blockDim.x) out_tile[e] = ws[e];
+    for (int e = head + body + threadIdx.x; e < N; e += blockDim.x) out_tile[e] = ws[e];
+  }
+  if (threadIdx.x == 0) bulk_wait<0, false>();
+}
+
 // ---------------------------------------------------------------------------
 // K3: interpolate k = K1 + K2 consecutive axes of a [hi][3^k][lo] array.
 // A CTA tile is all 3^k rows of L consecutive columns of one h.  Round 1
