@@ -508,10 +508,14 @@ def _timed_host_steps(one, min_steps, warmup, min_seconds=1.0, max_steps=100):
     one()
     t1 = time.perf_counter() - t0
     steps = max(min_steps, min(max_steps, int(min_seconds / max(t1, 1e-6)) + 1))
-    t0 = time.perf_counter()
+    per = []
     for _ in range(steps):
+        t0 = time.perf_counter()
         one()
-    return steps, time.perf_counter() - t0
+        per.append(time.perf_counter() - t0)
+    per.sort()
+    _timed_host_steps.last = {"step_ms_median": 1e3 * per[len(per) // 2], "step_ms_min": 1e3 * per[0]}
+    return steps, sum(per)
 
 
 def _e2e(wl, steps=3, warmup=1):
@@ -534,6 +538,7 @@ def _e2e(wl, steps=3, warmup=1):
 
     steps, dt = _timed_host_steps(one, steps, warmup)
     return {"value": wl.outputs * steps / dt, "unit": UNIT, "steps": steps,
+            **_timed_host_steps.last,
             "h2d_bytes_per_step": int(2 * x.nbytes), "d2h_bytes_per_step": int(zh.numel() * zh.element_size())}
 
 
@@ -542,20 +547,29 @@ def _e2e_other(wl, steps, warmup):
 
     hc = wl.hc
     if wl.name == "batched":
-        xh = [torch.from_numpy(x).pin_memory() for x, _ in wl.host_pairs]
-        yh = [torch.from_numpy(y).pin_memory() for _, y in wl.host_pairs]
-        zh = [torch.empty(3 ** d, dtype=torch.float32, pin_memory=True) for d in wl.dims]
-        h2d = sum(x.nbytes * 2 for x, _ in wl.host_pairs)
-        d2h = sum(4 * 3 ** d for d in wl.dims)
+        # the packed layout: all instances back to back in one page-locked
+        # array per operand, one copy each way (BatchedConv.from_packed)
+        import numpy as np
+
+        xo, nx = hc.packed_offsets(wl.dims, torch.float32, 2)
+        _, nz = hc.packed_offsets(wl.dims, torch.float32, 3)
+        xa = np.zeros(nx, np.float32)
+        ya = np.zeros(nx, np.float32)
+        for o, (x, y) in zip(xo, wl.host_pairs):
+            xa[o:o + x.size] = x
+            ya[o:o + y.size] = y
+        xh = torch.from_numpy(xa).pin_memory()
+        yh = torch.from_numpy(ya).pin_memory()
+        zh = torch.empty(nz, dtype=torch.float32, pin_memory=True)
+        b = hc.BatchedConv.from_packed(torch.empty(nx, dtype=torch.float32, device=wl.dev),
+                                       torch.empty(nx, dtype=torch.float32, device=wl.dev),
+                                       wl.dims, fused_max_d=wl.batch.fused_max_d)
+        b.capture()
+        h2d = 2 * 4 * nx
+        d2h = 4 * nz
 
         def one():
-            for i in range(len(xh)):
-                wl.xs[i].copy_(xh[i], non_blocking=True)
-                wl.ys[i].copy_(yh[i], non_blocking=True)
-            wl.batch.replay()
-            for i in range(len(zh)):
-                zh[i].copy_(wl.batch.outs[i].view(-1), non_blocking=True)
-            torch.cuda.synchronize()
+            b.run_host(xh, yh, zh)
     else:
         x, y, w = wl.host
         xh, yh, wh = (torch.from_numpy(a).pin_memory() for a in (x, y, w))
@@ -574,7 +588,8 @@ def _e2e_other(wl, steps, warmup):
             gyh.copy_(yd.grad, non_blocking=True)
             loss.item()
     steps, dt = _timed_host_steps(one, steps, warmup)
-    return {"value": wl.outputs * steps / dt, "unit": UNIT, "steps": steps, "h2d_bytes_per_step": int(h2d),
+    return {"value": wl.outputs * steps / dt, "unit": UNIT, "steps": steps, **_timed_host_steps.last,
+            "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
 
 

@@ -10,13 +10,14 @@ CUDA device (host tensors are copied to the device and back explicitly).
 from . import inputs  # noqa: F401  (numpy-only input generators)
 
 __all__ = ["inputs", "convolve", "convolve_backward", "convolve_batched", "BatchedConv",
-           "hypercube_conv", "HypercubeConv", "workspace_size", "carry_free_convolve", "build"]
+           "hypercube_conv", "HypercubeConv", "workspace_size", "carry_free_convolve", "packed_offsets",
+           "build"]
 
 
 def __getattr__(name):
     if name in ("convolve", "convolve_backward", "convolve_batched", "BatchedConv",
                 "hypercube_conv", "HypercubeConv", "workspace_size", "backward_workspace_size",
-                "dim_of", "HCError", "carry_free_convolve"):
+                "dim_of", "HCError", "carry_free_convolve", "packed_offsets"):
         from . import api
         return getattr(api, name)
     if name == "build":

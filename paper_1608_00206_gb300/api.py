@@ -224,6 +224,21 @@ def hypercube_conv(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
     return HypercubeConv.apply(x, y)
 
 
+def packed_offsets(dims, dtype: torch.dtype, base: int = 2):
+    """Offsets (elements) of the instances in a packed array of ``base``^D_i
+    elements per instance (2: inputs, 3: outputs).  Each offset is rounded up
+    to a multiple of 16 bytes, so that every instance's array is 16-byte
+    aligned (the library's rule) when the packed array is; returns
+    (offsets, total elements)."""
+    es = torch.empty((), dtype=dtype).element_size()
+    align = max(1, 16 // es)
+    offs, o = [], 0
+    for D in dims:
+        offs.append(o)
+        o += -(-(base ** int(D)) // align) * align
+    return offs, o
+
+
 class BatchedConv:
     """A prepared batch of independent convolutions (the batching form).
 
@@ -305,6 +320,45 @@ class BatchedConv:
             self.capture()
         self.graph.replay()
         return self.outs
+
+    @classmethod
+    def from_packed(cls, x_all: torch.Tensor, y_all: torch.Tensor, dims, *, mixed: bool = False,
+                    stream=None, fused_max_d=None):
+        """A batch whose instances live back to back in three arrays: x_all and
+        y_all (CUDA, 1-D, ``packed_offsets(dims, dtype, 2)`` layout) and the
+        outputs in ``self.z_all`` (``packed_offsets(dims, dtype, 3)``), so that
+        a whole batch moves between host and device in one copy per array
+        (:meth:`run_host`)."""
+        dims = [int(D) for D in dims]
+        dtype = x_all.dtype
+        xo, nx = packed_offsets(dims, dtype, 2)
+        zo, nz = packed_offsets(dims, dtype, 3)
+        if x_all.dim() != 1 or y_all.shape != x_all.shape or y_all.dtype != dtype \
+                or x_all.numel() < nx:
+            raise ValueError("x_all, y_all must be 1-D arrays of one dtype in the packed layout")
+        xs = [x_all[o:o + (1 << D)] for o, D in zip(xo, dims)]
+        ys = [y_all[o:o + (1 << D)] for o, D in zip(xo, dims)]
+        z_all = torch.empty(max(nz, 1), dtype=dtype, device=x_all.device)
+        outs = [z_all[o:o + 3 ** D] for o, D in zip(zo, dims)]
+        self = cls(xs, ys, outs, mixed=mixed, stream=stream, fused_max_d=fused_max_d)
+        self.x_all, self.y_all, self.z_all = x_all, y_all, z_all
+        return self
+
+    def run_host(self, xh: torch.Tensor, yh: torch.Tensor, zh: torch.Tensor) -> torch.Tensor:
+        """One batch from page-locked host arrays in the packed layout of a
+        :meth:`from_packed` batch: copy x and y in, replay the captured batch,
+        copy z out (one copy each, on the current stream), then synchronise."""
+        if not hasattr(self, "z_all"):
+            raise ValueError("run_host needs a batch made by BatchedConv.from_packed")
+        if xh.shape != self.x_all.shape or yh.shape != self.y_all.shape or \
+                zh.shape != self.z_all.shape:
+            raise ValueError("host arrays must have the packed shapes of x_all, y_all, z_all")
+        self.x_all.copy_(xh, non_blocking=True)
+        self.y_all.copy_(yh, non_blocking=True)
+        self.replay()
+        zh.copy_(self.z_all, non_blocking=True)
+        torch.cuda.current_stream(self.device).synchronize()
+        return zh
 
     def status(self) -> int:
         """Synchronises and returns the workspace status word (0 = HC_OK)."""

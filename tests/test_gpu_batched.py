@@ -138,3 +138,41 @@ def test_batched_rejects_bad_instances(hc):
     x = T(np.zeros(1 << 16, np.int64))
     with pytest.raises(ValueError):
         hc.BatchedConv([x], [x])  # D = 16 int64 exceeds the batched limit
+
+
+@pytest.mark.parametrize("kind", ["int64", "float32", "mixed"])
+def test_packed_batch_from_host(hc, kind):
+    """BatchedConv.from_packed + run_host: every instance's array sits at a
+    16-byte-aligned offset of one packed array (odd sizes, so most offsets
+    carry padding), the batch moves in one copy per array, and every
+    instance is bitwise the oracle's result, twice in a row (graph replay on
+    new host inputs)."""
+    dims = [0, 1, 2, 3, 5, 7, 9, 11, 12, 13, 3, 1]
+    dt = np.int64 if kind == "int64" else np.float32
+    tdt = torch.int64 if kind == "int64" else torch.float32
+    xo, nx = hc.packed_offsets(dims, tdt, 2)
+    zo, nz = hc.packed_offsets(dims, tdt, 3)
+    xh = torch.zeros(nx, dtype=tdt).pin_memory()
+    yh = torch.zeros(nx, dtype=tdt).pin_memory()
+    zh = torch.empty(nz, dtype=tdt).pin_memory()
+    b = hc.BatchedConv.from_packed(torch.zeros(nx, dtype=tdt, device=DEV),
+                                   torch.zeros(nx, dtype=tdt, device=DEV), dims,
+                                   mixed=(kind == "mixed"))
+    for rep in range(2):
+        pairs = []
+        for i, D in enumerate(dims):
+            if kind == "int64":
+                x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=100 * rep + i)
+            else:
+                x, y = inputs.uniform01_pair(D, seed=100 * rep + i)
+            pairs.append((x, y))
+            xh[xo[i]:xo[i] + (1 << D)] = torch.from_numpy(x.astype(dt))
+            yh[xo[i]:xo[i] + (1 << D)] = torch.from_numpy(y.astype(dt))
+        b.run_host(xh, yh, zh)
+        z = zh.numpy()
+        for i, ((x, y), D) in enumerate(zip(pairs, dims)):
+            want = oracle.convolve_mixed(x, y) if kind == "mixed" else oracle.convolve(x, y)
+            got = z[zo[i]:zo[i] + 3 ** D]
+            assert np.array_equal(bits(got.copy()), bits(want)), f"rep {rep} D={D}"
+    with pytest.raises(ValueError):
+        b.run_host(xh[:-1], yh, zh)
