@@ -176,6 +176,162 @@ inline size_t tile_smem_bytes(hc_dtype dt, int C) {
   return 0;
 }
 
+// The stages of a tile of G >= 2 groups, one pencil per call (tile_body and
+// the pipelined bulk loop run them; see tile_body for the order).  smem: the
+// tile's TileSmem<M, C>::bytes.
+template <class M, int C>
+struct TileStages {
+  typedef typename M::In In;
+  typedef typename M::W W;
+  typedef typename M::Out Out;
+  typedef TileShape<C> S;
+  static constexpr int LP = TileSmem<M, C>::LP;  // row stride of LastX, LastY
+  static constexpr int kStage0 = 2 * p2(C - S::g0);   // stage-0 pencils
+  static constexpr int kInterp0 = p3(C - S::g0);      // last-stage pencils
+  static __device__ __forceinline__ In* last_x(unsigned char* smem) {
+    return reinterpret_cast<In*>(smem + TileSmem<M, C>::kLastOff);
+  }
+
+  // stage 0, pencil p: evaluate group 0 (g0 axes) from the operand rows
+  template <class Loader>
+  static __device__ __forceinline__ void stage0(const Loader& ld, unsigned char* smem, int p) {
+    constexpr int R = p2(C - S::g0);  // pencils per operand
+    const int op = p / R, r = p - op * R;
+    In v[p3(S::g0)];
+#pragma unroll
+    for (int b = 0; b < p2(S::g0); ++b) v[b] = ld(op, b * R + r);
+    eval_pencil<M, S::g0>(v);
+    if constexpr (S::G == 2) {
+      // next is the fused stage: transposed [2^gL][3^g0], r = last-group bits
+      In* d = last_x(smem) + op * (p2(S::gL) * LP);
+#pragma unroll
+      for (int j = 0; j < p3(S::g0); ++j) d[r * p3(S::g0) + j] = v[j];
+    } else {
+      constexpr int S1R = TileSmem<M, C>::S1R;
+      In* d = reinterpret_cast<In*>(smem) + op * (p3(S::g0) * S1R);  // S1 aliases the W tile
+#pragma unroll
+      for (int j = 0; j < p3(S::g0); ++j) d[j * S1R + r] = v[j];
+    }
+  }
+
+  // stage 1 (G == 3): evaluate group 1 (3 axes) in shared memory, all pencils
+  static __device__ __forceinline__ void stage1(unsigned char* smem) {
+    constexpr int O = p3(S::g0);
+    constexpr int R = p2(S::gL);  // remaining binary axes (innermost group)
+    constexpr int NP = O * R;
+    constexpr int S1R = TileSmem<M, C>::S1R;  // = 8 * R + padding
+    const In* S1 = reinterpret_cast<const In*>(smem);
+    In* LastX = last_x(smem);
+    In* LastY = LastX + p2(S::gL) * LP;
+#pragma unroll 1
+    for (int p = threadIdx.x; p < 2 * NP; p += blockDim.x) {
+      const int op = p / NP, q = p - op * NP;
+      const int o = q / R, r = q - o * R;
+      const In* s = S1 + op * (O * S1R);
+      In v[27];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) v[b] = s[o * S1R + b * R + r];
+      eval_pencil<M, 3>(v);
+      In* d = op ? LastY : LastX;
+#pragma unroll
+      for (int j = 0; j < 27; ++j) d[r * LP + o * 27 + j] = v[j];
+    }
+  }
+
+  // fused stage: evaluate the innermost group, multiply, interpolate it.
+  // With the stage buffers inside the W tile (kAlias) every thread reads its
+  // one pencil's inputs, a barrier follows, then W is written.
+  static __device__ __forceinline__ void fused(unsigned char* smem) {
+    constexpr int NO = S::nLastPencils;
+    W* Ws = reinterpret_cast<W*>(smem);
+    const In* LastX = last_x(smem);
+    const In* LastY = LastX + p2(S::gL) * LP;
+    if constexpr (TileSmem<M, C>::kAlias) {
+      const int o = threadIdx.x;
+      In a[27], b[27];
+      if (o < NO) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          a[q] = LastX[q * LP + o];
+          b[q] = LastY[q * LP + o];
+        }
+      }
+      __syncthreads();
+      if (o < NO) {
+        eval_pencil<M, 3>(a);
+        eval_pencil<M, 3>(b);
+        W w[27];
+#pragma unroll
+        for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
+        interp_pencil<M, 3>(w);
+#pragma unroll
+        for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
+      }
+    } else {
+#pragma unroll 1
+      for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+        In a[27], b[27];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          a[q] = LastX[q * LP + o];
+          b[q] = LastY[q * LP + o];
+        }
+        eval_pencil<M, 3>(a);
+        eval_pencil<M, 3>(b);
+        W w[27];
+#pragma unroll
+        for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
+        interp_pencil<M, 3>(w);
+#pragma unroll
+        for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
+      }
+    }
+  }
+
+  // interpolate group 1 (G == 3) in shared memory, all pencils.  The group-0
+  // digit o runs fastest across threads: lanes then never straddle two
+  // 27-element runs of one o, whose banks would overlap.
+  static __device__ __forceinline__ void interp1(unsigned char* smem) {
+    constexpr int O = p3(S::g0), R = 27;
+    W* Ws = reinterpret_cast<W*>(smem);
+#pragma unroll 1
+    for (int p = threadIdx.x; p < O * R; p += blockDim.x) {
+      const int r = p / O, o = p - r * O;
+      W v[27];
+#pragma unroll
+      for (int j = 0; j < 27; ++j) v[j] = Ws[(o * 27 + j) * R + r];
+      interp_pencil<M, 3>(v);
+#pragma unroll
+      for (int j = 0; j < 27; ++j) Ws[(o * 27 + j) * R + r] = v[j];
+    }
+  }
+
+  // last stage, pencil r: interpolate group 0 and write the outputs to
+  // out_tile (global), or back into the W tile (SMEM_OUT)
+  template <bool FINAL, bool SMEM_OUT>
+  static __device__ __forceinline__ void interp0(void* __restrict__ out_tile, unsigned char* smem,
+                                                 int r) {
+    constexpr int R = p3(C - S::g0);
+    W* Ws = reinterpret_cast<W*>(smem);
+    W v[p3(S::g0)];
+#pragma unroll
+    for (int j = 0; j < p3(S::g0); ++j) v[j] = Ws[j * R + r];
+    interp_pencil<M, S::g0>(v);
+    if constexpr (SMEM_OUT) {
+#pragma unroll
+      for (int j = 0; j < p3(S::g0); ++j) Ws[j * R + r] = v[j];
+    } else if constexpr (FINAL) {
+      Out* o = reinterpret_cast<Out*>(out_tile);
+#pragma unroll
+      for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = M::out(v[j]);
+    } else {
+      W* o = reinterpret_cast<W*>(out_tile);
+#pragma unroll
+      for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = v[j];
+    }
+  }
+};
+
 // SMEM_OUT (intermediate tiles only, FINAL false): the last stage writes the
 // finished tile back into the W tile in shared memory (in place, each thread
 // its own pencils; out_tile unused) and fences it for the async proxy, so
@@ -187,177 +343,55 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
   typedef typename M::W W;
   typedef typename M::Out Out;
   typedef TileShape<C> S;
-  W* Ws = reinterpret_cast<W*>(smem);
-  constexpr int LP = TileSmem<M, C>::LP;  // row stride of LastX, LastY
-  In* LastX = reinterpret_cast<In*>(smem + TileSmem<M, C>::kLastOff);
-  In* LastY = LastX + p2(S::gL) * LP;
-  In* S1 = reinterpret_cast<In*>(smem);  // G == 3 only; aliases the W tile
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
-
-  {
-    if constexpr (S::G == 1) {
-      // C <= 3: one pencil, straight from global to global.
-      if (tid == 0) {
-        In a[p3(C)], b[p3(C)];
+  if constexpr (S::G == 1) {
+    // C <= 3: one pencil, straight from global to global.
+    if (tid == 0) {
+      In a[p3(C)], b[p3(C)];
 #pragma unroll
-        for (int i = 0; i < p2(C); ++i) {
-          a[i] = ld(0, i);
-          b[i] = ld(1, i);
-        }
-        eval_pencil<M, C>(a);
-        eval_pencil<M, C>(b);
-        W w[p3(C)];
-#pragma unroll
-        for (int j = 0; j < p3(C); ++j) w[j] = M::mul(a[j], b[j]);
-        interp_pencil<M, C>(w);
-        if constexpr (FINAL) {
-          Out* o = reinterpret_cast<Out*>(out_tile);
-#pragma unroll
-          for (int j = 0; j < p3(C); ++j) o[j] = M::out(w[j]);
-        } else {
-          W* o = reinterpret_cast<W*>(out_tile);
-#pragma unroll
-          for (int j = 0; j < p3(C); ++j) o[j] = w[j];
-        }
+      for (int i = 0; i < p2(C); ++i) {
+        a[i] = ld(0, i);
+        b[i] = ld(1, i);
       }
-    } else {
-      // ---- stage 0: evaluate group 0 (g0 axes) from global memory.
-      {
-        constexpr int R = p2(C - S::g0);  // pencils per operand
-        #pragma unroll 1
-        for (int p = tid; p < 2 * R; p += nt) {
-          const int op = p / R, r = p - op * R;
-          In v[p3(S::g0)];
+      eval_pencil<M, C>(a);
+      eval_pencil<M, C>(b);
+      W w[p3(C)];
 #pragma unroll
-          for (int b = 0; b < p2(S::g0); ++b) v[b] = ld(op, b * R + r);
-          eval_pencil<M, S::g0>(v);
-          if constexpr (S::G == 2) {
-            // next is the fused stage: transposed [2^gL][3^g0], r = last-group bits
-            In* d = op ? LastY : LastX;
+      for (int j = 0; j < p3(C); ++j) w[j] = M::mul(a[j], b[j]);
+      interp_pencil<M, C>(w);
+      if constexpr (FINAL) {
+        Out* o = reinterpret_cast<Out*>(out_tile);
 #pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) d[r * p3(S::g0) + j] = v[j];
-          } else {
-            constexpr int S1R = TileSmem<M, C>::S1R;
-            In* d = S1 + op * (p3(S::g0) * S1R);
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) d[j * S1R + r] = v[j];
-          }
-        }
-      }
-      __syncthreads();
-      // ---- stage 1 (G == 3): evaluate group 1 (3 axes) in shared memory.
-      if constexpr (S::G == 3) {
-        constexpr int O = p3(S::g0);
-        constexpr int R = p2(S::gL);  // remaining binary axes (innermost group)
-        constexpr int NP = O * R;
-        constexpr int S1R = TileSmem<M, C>::S1R;  // = 8 * R + padding
-        #pragma unroll 1
-        for (int p = tid; p < 2 * NP; p += nt) {
-          const int op = p / NP, q = p - op * NP;
-          const int o = q / R, r = q - o * R;
-          const In* s = S1 + op * (O * S1R);
-          In v[27];
-#pragma unroll
-          for (int b = 0; b < 8; ++b) v[b] = s[o * S1R + b * R + r];
-          eval_pencil<M, 3>(v);
-          In* d = op ? LastY : LastX;
-#pragma unroll
-          for (int j = 0; j < 27; ++j) d[r * LP + o * 27 + j] = v[j];
-        }
-        __syncthreads();
-      }
-      // ---- fused stage: evaluate innermost group, multiply, interpolate it.
-      if constexpr (TileSmem<M, C>::kAlias) {
-        // one pencil per thread; all inputs are read before W is written
-        constexpr int NO = S::nLastPencils;
-        const int o = tid;
-        In a[27], b[27];
-        if (o < NO) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            a[q] = LastX[q * LP + o];
-            b[q] = LastY[q * LP + o];
-          }
-        }
-        __syncthreads();
-        if (o < NO) {
-          eval_pencil<M, 3>(a);
-          eval_pencil<M, 3>(b);
-          W w[27];
-#pragma unroll
-          for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
-          interp_pencil<M, 3>(w);
-#pragma unroll
-          for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
-        }
+        for (int j = 0; j < p3(C); ++j) o[j] = M::out(w[j]);
       } else {
-        constexpr int NO = S::nLastPencils;
-        #pragma unroll 1
-        for (int o = tid; o < NO; o += nt) {
-          In a[27], b[27];
+        W* o = reinterpret_cast<W*>(out_tile);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            a[q] = LastX[q * LP + o];
-            b[q] = LastY[q * LP + o];
-          }
-          eval_pencil<M, 3>(a);
-          eval_pencil<M, 3>(b);
-          W w[27];
-#pragma unroll
-          for (int j = 0; j < 27; ++j) w[j] = M::mul(a[j], b[j]);
-          interp_pencil<M, 3>(w);
-#pragma unroll
-          for (int j = 0; j < 27; ++j) Ws[o * 27 + j] = w[j];
-        }
+        for (int j = 0; j < p3(C); ++j) o[j] = w[j];
       }
-      __syncthreads();
-      // ---- interpolate group 1 (G == 3) in shared memory.  The group-0
-      // digit o runs fastest across threads: lanes then never straddle two
-      // 27-element runs of one o, whose banks would overlap.
-      if constexpr (S::G == 3) {
-        constexpr int O = p3(S::g0), R = 27;
-        #pragma unroll 1
-        for (int p = tid; p < O * R; p += nt) {
-          const int r = p / O, o = p - r * O;
-          W v[27];
-#pragma unroll
-          for (int j = 0; j < 27; ++j) v[j] = Ws[(o * 27 + j) * R + r];
-          interp_pencil<M, 3>(v);
-#pragma unroll
-          for (int j = 0; j < 27; ++j) Ws[(o * 27 + j) * R + r] = v[j];
-        }
-        __syncthreads();
-      }
-      // ---- interpolate group 0 and write the tile to global memory.
-      {
-        constexpr int R = p3(C - S::g0);
-        #pragma unroll 1
-        for (int r = tid; r < R; r += nt) {
-          W v[p3(S::g0)];
-#pragma unroll
-          for (int j = 0; j < p3(S::g0); ++j) v[j] = Ws[j * R + r];
-          interp_pencil<M, S::g0>(v);
-          if constexpr (SMEM_OUT) {
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) Ws[j * R + r] = v[j];
-          } else if constexpr (FINAL) {
-            Out* o = reinterpret_cast<Out*>(out_tile);
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = M::out(v[j]);
-          } else {
-            W* o = reinterpret_cast<W*>(out_tile);
-#pragma unroll
-            for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = v[j];
-          }
-        }
-      }
-      if constexpr (SMEM_OUT) {
-        static_assert(!FINAL, "bulk tile stores write the intermediate W");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      }
-      __syncthreads();  // the caller's next tile reuses shared memory
     }
+  } else {
+    typedef TileStages<M, C> St;
+#pragma unroll 1
+    for (int p = tid; p < St::kStage0; p += nt) St::stage0(ld, smem, p);
+    __syncthreads();
+    if constexpr (S::G == 3) {
+      St::stage1(smem);
+      __syncthreads();
+    }
+    St::fused(smem);
+    __syncthreads();
+    if constexpr (S::G == 3) {
+      St::interp1(smem);
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int r = tid; r < St::kInterp0; r += nt) St::template interp0<FINAL, SMEM_OUT>(out_tile, smem, r);
+    if constexpr (SMEM_OUT) {
+      static_assert(!FINAL, "bulk tile stores write the intermediate W");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();  // the caller's next tile reuses shared memory
   }
 }
 
@@ -368,8 +402,11 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
 // otherwise bunch up the tile's whole output at its end).  The W buffer is
 // placed at the output's address modulo 16, so that shared and global
 // addresses agree in their low bits; the elements before the output's first
-// 16-byte boundary and after its last are stored by threads.  The next
-// tile's rows are prefetched with cp.async.  src(t, op): tile t's operand row
+// 16-byte boundary and after its last are stored by threads.  The tiles are
+// pipelined one stage deep: the next tile's stage 0 (from its rows,
+// prefetched with cp.async) runs in the other W buffer in the same barrier
+// interval as this tile's last stage, which fills the threads stage 0 leaves
+// idle and saves two barriers per tile.  src(t, op): tile t's operand row
 // (op 0 = x, 1 = y), 2^C elements; out(t): tile t's 3^C outputs, in a plain
 // device allocation.  smem: TileBulk<M, C>::bytes.  Tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...
@@ -378,46 +415,91 @@ __device__ __forceinline__ void tile_loop_bulk(SrcFn src, OutFn out, long long n
                                                unsigned char* smem) {
   typedef typename M::In In;
   typedef typename M::W W;
-  static_assert(TileShape<C>::G >= 2, "bulk tiles: C >= 4");
+  typedef TileShape<C> S;
+  static_assert(S::G >= 2, "bulk tiles: C >= 4");
   typedef TileBulk<M, C> B;
+  typedef TileStages<M, C> St;
   constexpr int N = p3(C);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long step = gridDim.x;
   In* rows = reinterpret_cast<In*>(smem + B::kOff);  // [buffer][operand][2^C]
   auto prefetch = [&](long long t, int b) {
 #pragma unroll 1
-    for (int e = threadIdx.x; e < 2 * p2(C); e += blockDim.x) {
+    for (int e = tid; e < 2 * p2(C); e += nt) {
       const int op = e >> C, i = e & (p2(C) - 1);
       cp_async<sizeof(In)>(rows + (b * 2 + op) * p2(C) + i, src(t, op) + i);
     }
     cp_async_commit();
   };
-  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0);
-  int it = 0;
+  // tile t's W tile in buffer b, at its output's address modulo 16
+  auto wtile = [&](long long t, int b) {
+    return smem + b * B::kWB + (unsigned)(reinterpret_cast<uintptr_t>(out(t)) & 15);
+  };
+  long long t = blockIdx.x;
+  if (t >= ntiles) return;
+  prefetch(t, 0);
+  if (t + step < ntiles) {
+    prefetch(t + step, 1);
+    cp_async_wait<1>();
+  } else {
+    cp_async_wait<0>();
+  }
+  __syncthreads();  // the first tile's rows are in buffer 0
+  {
+    RowLoader<In> ld{rows, rows + p2(C)};
+    unsigned char* w0 = wtile(t, 0);
 #pragma unroll 1
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it ^= 1) {
-    if (t + gridDim.x < ntiles) {
-      prefetch(t + gridDim.x, it ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    for (int p = tid; p < St::kStage0; p += nt) St::stage0(ld, w0, p);
+  }
+  __syncthreads();
+  int b = 0;
+#pragma unroll 1
+  for (; t < ntiles; t += step, b ^= 1) {
+    unsigned char* w = wtile(t, b);
+    const long long tn = t + step;
+    const bool next = tn < ntiles;
+    if constexpr (S::G == 3) {
+      St::stage1(w);
+      __syncthreads();
     }
-    // the copy issued from buffer `it` two tiles ago has read its source
-    if (threadIdx.x == 0) bulk_wait<1, true>();
-    __syncthreads();  // this tile's rows are in buffer `it`; W buffer `it` is free
+    St::fused(w);
+    if constexpr (S::G == 3) {
+      __syncthreads();
+      St::interp1(w);
+    }
+    // before the barrier that opens the last stage: the next tile's rows have
+    // landed, and the copy of tile t - step has read the other W buffer
+    if (next) cp_async_wait<0>();
+    if (tid == 0) bulk_wait<0, true>();
+    __syncthreads();
+    // last stage of tile t and stage 0 of tile tn, one barrier interval
+    {
+      RowLoader<In> ld{rows + ((b ^ 1) * 2) * p2(C), rows + ((b ^ 1) * 2 + 1) * p2(C)};
+      unsigned char* wn = next ? wtile(tn, b ^ 1) : nullptr;
+      const int items = St::kInterp0 + (next ? St::kStage0 : 0);
+#pragma unroll 1
+      for (int p = tid; p < items; p += nt) {
+        if (p < St::kInterp0)
+          St::template interp0<false, true>(nullptr, w, p);
+        else
+          St::stage0(ld, wn, p - St::kInterp0);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    // tile t is in w[0, N): head / body / tail split at 16-byte boundaries
     W* out_tile = out(t);
     const unsigned mis = (unsigned)(reinterpret_cast<uintptr_t>(out_tile) & 15);
-    unsigned char* wb = smem + it * B::kWB + mis;
-    RowLoader<In> ld{rows + (it * 2 + 0) * p2(C), rows + (it * 2 + 1) * p2(C)};
-    tile_body<M, C, false, RowLoader<In>, true>(ld, nullptr, wb);
-    // the tile is in wb[0, N), fenced; head / body / tail split at 16-byte boundaries
     const int head = mis ? (int)((16 - mis) / sizeof(W)) : 0;
     const int body = (int)(((N - head) * sizeof(W)) / 16 * 16 / sizeof(W));
-    const W* ws = reinterpret_cast<const W*>(wb);
-    if (threadIdx.x == 0 && body > 0)
-      bulk_store(out_tile + head, ws + head, (unsigned)(body * sizeof(W)));
-    for (int e = threadIdx.x; e < head; e += blockDim.x) out_tile[e] = ws[e];
-    for (int e = head + body + threadIdx.x; e < N; e += blockDim.x) out_tile[e] = ws[e];
+    const W* ws = reinterpret_cast<const W*>(w);
+    if (tid == 0 && body > 0) bulk_store(out_tile + head, ws + head, (unsigned)(body * sizeof(W)));
+    for (int e = tid; e < head; e += nt) out_tile[e] = ws[e];
+    for (int e = head + body + tid; e < N; e += nt) out_tile[e] = ws[e];
+    // rows buffer b was consumed by this tile's stage 0, one iteration ago
+    if (tn + step < ntiles) prefetch(tn + step, b);
   }
-  if (threadIdx.x == 0) bulk_wait<0, false>();
+  if (tid == 0) bulk_wait<0, false>();
 }
 
 // ---------------------------------------------------------------------------
