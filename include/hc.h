@@ -100,6 +100,10 @@ const char* hc_last_cuda_error(void);
  *
  * hc_convolve: z = x * y.  x, y: 2^D elements; z: 3^D elements; all of the
  * dtype's element type (int64, double or float; float for HC_FP32_MIXED).
+ * z may be a plain device allocation or managed memory: the call asks the
+ * runtime (cudaPointerGetAttributes) which one it is, and only into a plain
+ * device allocation are whole tiles stored with bulk (TMA engine) copies;
+ * the results are the same bits either way.
  */
 size_t hc_workspace_size(int D, hc_dtype dtype);
 
@@ -244,7 +248,10 @@ hc_status hc_convolve_backward(const void* dz, const void* x, const void* y, voi
  * hc_batched_prepare builds the work list on the host, copies it into the
  * workspace and synchronises `stream` (so it cannot be captured; the host
  * array may be reused on return).  It remembers the plan under the workspace
- * address for later launches.
+ * address for later launches.  It also asks the runtime once per instance
+ * whether its output (its intermediate, for the grouped form) is a plain
+ * device allocation; the groups whose arrays all are store their tiles with
+ * bulk copies.
  * hc_batched_launch only resets counters and launches, so it can be captured
  * in a CUDA graph and replayed; every replay recomputes the prepared batch.
  * Device-side waits are bounded: a wait that gives up records HC_ERR_TIMEOUT
