@@ -176,6 +176,7 @@ class Workload:
 
         self.name = name
         self.dev = dev
+        self.D_override = D_override
         self.sched = {}
         self.hc = hc
         self.torch = torch
@@ -697,6 +698,114 @@ def _dtype_name(w):
 # ------------------------------------------------------------------- main
 
 
+def _roofline(wl, prof, steps):
+    """Roofline of the kernel with the largest traced device time: its
+    algorithmic bytes (or FP64 operations) per launch over its mean launch
+    time, against the measured HBM peak (or the FP64 roof)."""
+    peak_hbm, peak_kind = _peaks()
+    if not prof:
+        return None
+    kname, (launches, kms) = max(prof.items(), key=lambda kv: kv[1][1])
+    lps = launches / steps
+    alg, bound = wl.kernel_alg(kname, lps)
+    per_launch_ms = kms / launches
+    if alg is None:
+        return {"bound": "hbm", "kernel": kname, "achieved": None, "peak": peak_hbm,
+                "unit": "GB/s", "frac": None, "traffic": None}
+    if bound == "alu":
+        achieved = alg / (per_launch_ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": kname, "achieved": achieved,
+                "peak": FP64_OPS_PEAK / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (FP64_OPS_PEAK / 1e12), "traffic": None,
+                "ms_per_launch": per_launch_ms,
+                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2)"}
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_hbm,
+            "unit": "GB/s", "frac": achieved / peak_hbm,
+            "traffic": _traffic_from_profiles(wl.name if wl.D_override is None else
+                                              f"{wl.name}@D{wl.D}", kname),
+            "ms_per_launch": per_launch_ms,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def _measure(wl, steps, warmup, dist, world):
+    """Time `steps` steps of a prepared workload; the per-workload part of the
+    JSON line (time, value, roofline, kernels, clocks)."""
+    ms, prof, clk = _time_steps(wl, steps, warmup, dist)
+    peak_hbm, _ = _peaks()
+    return {
+        "ms_per_step": ms / steps,
+        "value": _whole_job_value(world, wl.outputs, steps, ms),
+        "steps": steps,
+        "roofline": _roofline(wl, prof, steps),
+        "alg_hbm_frac": (wl.alg_bytes * steps / (ms / 1e3) / 1e9) / peak_hbm,
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()},
+        "gpu_launches": sum(v[0] for v in prof.values()),
+        "clocks": clk,
+    }
+
+
+# D = 14..19 of the D = 20 int64 workload (same value distribution, tuned
+# schedules): steps per D so that each point takes a fraction of a second.
+SWEEP_STEPS = {14: 200, 15: 100, 16: 60, 17: 40, 18: 30, 19: 20}
+# The training-system forms beside the plain method, each timed after the
+# headline: (workload, steps).
+FORMS = (("batched", 20), ("fwdbwd", 30), ("d16_fp64", 30), ("d16_mixed", 50),
+         ("d18_fp32", 50))
+
+
+def _brief(res):
+    r = res.get("roofline") or {}
+    out = {"ms_per_step": round(res["ms_per_step"], 5), "value": res["value"],
+           "alg_hbm_frac": round(res["alg_hbm_frac"], 4),
+           "dominant": {k: (round(v, 4) if isinstance(v, float) else v)
+                        for k, v in r.items() if k in ("kernel", "bound", "achieved", "frac",
+                                                       "peak", "unit", "ms_per_launch",
+                                                       "traffic")},
+           "kernels": res["kernels"], "gpu_launches": res["gpu_launches"],
+           "clocks": res["clocks"]}
+    return out
+
+
+def _sweep(dev, main_res, main_D, warmup):
+    """D = 14..20 int64 (the D = 20 workload's distribution, tuned schedules):
+    per D the step time, outputs/s, the whole-method algorithmic fraction and
+    the dominant kernel's roofline."""
+    import torch
+    out = {}
+    for D in sorted(SWEEP_STEPS):
+        if D == main_D:
+            continue
+        wl = Workload("d20_int64", dev, 0, D)
+        res = _measure(wl, SWEEP_STEPS[D], warmup, None, 1)
+        out[str(D)] = {"outputs": 3 ** D, **_brief(res)}
+        del wl
+        torch.cuda.empty_cache()
+    out[str(main_D)] = {"outputs": 3 ** main_D, **_brief(main_res)}
+    return dict(sorted(out.items(), key=lambda kv: int(kv[0])))
+
+
+def _forms(dev, warmup):
+    """The batched, differentiation and precision forms, each timed on its
+    own after the headline, with its comparison against the plain method."""
+    import torch
+    out = {}
+    for name, steps in FORMS:
+        wl = Workload(name, dev, 0, None)
+        res = _measure(wl, steps, warmup, None, 1)
+        entry = {"workload": WORKLOADS[name], "dtype": _dtype_name(name),
+                 "outputs_per_step": wl.outputs, **_brief(res)}
+        if name == "batched":
+            entry["fused_max_d"] = wl.batch.fused_max_d
+        cmp = _comparisons(wl, res["ms_per_step"])
+        if cmp is not None:
+            entry["comparisons"] = cmp
+        out[name] = entry
+        del wl
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -706,6 +815,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the D=14..19 sweep and the forms after the D=20 headline")
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
@@ -755,36 +866,14 @@ def main():
         wl.ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
     if args.workload == "d10_int64":
         wl.use_graph()  # launch-bound: replay the convolution from a CUDA graph
-    ms, prof, clk = _time_steps(wl, args.steps, args.warmup, dist)
-    value = _whole_job_value(world, wl.outputs, args.steps, ms)
+    res = _measure(wl, args.steps, args.warmup, dist, world)
+    ms = res["ms_per_step"] * args.steps
 
-    # roofline of the dominant kernel (largest device time in the timed region)
-    peak_hbm, peak_kind = _peaks()
-    roof = None
-    if prof:
-        kname, (launches, kms) = max(prof.items(), key=lambda kv: kv[1][1])
-        lps = launches / args.steps
-        alg, bound = wl.kernel_alg(kname, lps)
-        per_launch_ms = kms / launches
-        if alg is not None:
-            if bound == "alu":
-                achieved = alg / (per_launch_ms / 1e3) / 1e12
-                roof = {"bound": "alu", "kernel": kname, "achieved": achieved,
-                        "peak": FP64_OPS_PEAK / 1e12, "unit": "TFLOP/s",
-                        "frac": achieved / (FP64_OPS_PEAK / 1e12), "traffic": None,
-                        "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2)"}
-            else:
-                achieved = alg / (per_launch_ms / 1e3) / 1e9
-                roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_hbm,
-                        "unit": "GB/s", "frac": achieved / peak_hbm,
-                        "traffic": _traffic_from_profiles(args.workload, kname),
-                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
-    launches = sum(v[0] for v in prof.values())
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": _dtype_name(args.workload),
-        "data": "synthetic",
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": _dtype_name(args.workload), "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] if args.D is None else
                    f"{WORKLOADS[args.workload]} with D overridden to {args.D}",
                    "schedule": args.schedule or "tuned default",
@@ -799,11 +888,11 @@ def main():
                    if wl.alg_bytes >= L2_BYTES else
                    "working set below L2: L2 flushed between steps (256 MB write, "
                    "outside the per-step CUDA events; time = sum of the steps' events)"},
-        "roofline": roof,
-        "alg_hbm_frac": (wl.alg_bytes * args.steps / (ms / 1e3) / 1e9) / peak_hbm,
-        "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()},
-        "gpu_launches": launches,
-        "clocks": clk,
+        "roofline": res["roofline"],
+        "alg_hbm_frac": res["alg_hbm_frac"],
+        "kernels": res["kernels"],
+        "gpu_launches": res["gpu_launches"],
+        "clocks": res["clocks"],
     }
     if world == 1:
         cmp = _comparisons(wl, ms / args.steps)
@@ -813,6 +902,12 @@ def main():
         line["e2e"] = _e2e(wl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(args.workload)
+    headline_default = (args.workload == "d20_int64" and args.D is None and not args.schedule)
+    if world == 1 and headline_default and not args.no_sweep:
+        del wl
+        torch.cuda.empty_cache()
+        line["sweep"] = _sweep(dev, res, 20, args.warmup)
+        line["forms"] = _forms(dev, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

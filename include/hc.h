@@ -189,6 +189,34 @@ hc_status hc_convolve_out(const void* x, const void* y, void* w, void* z, int D,
                           void* workspace, size_t ws_bytes, hc_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Carry-free 1D convolution (Discussion: "carry-free convolution" solved by
+ * embedding into a hypercube).  For vectors x, y of N >= 1 elements:
+ *     z[k] = sum of x[i] * y[j] over the pairs (i, j) whose bits, added
+ *            position by position without carries, give the base-3 digits
+ *            of k,
+ * with D = ceil(log2 N) digits (D = 0 for N = 1), most significant first.
+ * Example (Discussion): i = 7 = (1,1,1), j = 5 = (1,0,1) contribute to
+ * digits (2,1,2), z[23], not to the carried sum 12.  Reading bit d of an
+ * index as axis d, this is hc_convolve of x and y zero-padded to 2^D
+ * elements, which is how it is computed: a library kernel writes the padded
+ * copies into the workspace, then the plain form runs on them (same
+ * schedule, kernels and bits as hc_convolve).
+ *   x, y : N elements of the dtype's type, device memory, 16-byte aligned;
+ *          const.
+ *   z    : 3^D elements, fully overwritten; entries whose digits no pair
+ *          reaches (possible when N < 2^D) are zero.
+ *   workspace: hc_carryfree_workspace_size(N, dtype) bytes, 256-byte aligned
+ *          (for N a power of two this is hc_workspace_size(D, dtype) and no
+ *          copy is made).
+ * Errors: HC_ERR_ARG for N = 0, D > HC_MAX_D or a NULL pointer; the plain
+ * form's alignment, aliasing and workspace rules otherwise.
+ * hc_carryfree_workspace_size returns 0 for an invalid (N, dtype). */
+size_t hc_carryfree_workspace_size(size_t N, hc_dtype dtype);
+
+hc_status hc_carryfree(const void* x, const void* y, void* z, size_t N, hc_dtype dtype,
+                       void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * No-allocation form.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory at the call site -- code
  * running while another framework owns the device's memory pool,
@@ -202,11 +230,15 @@ hc_status hc_convolve_out(const void* x, const void* y, void* w, void* z, int D,
  *     is installed).  Limit: a problem whose workspace for that schedule
  *     exceeds the array is refused with HC_ERR_WORKSPACE.  With 16 MiB that allows D <= 16 for HC_INT64
  *     and HC_FP64, D <= 17 for HC_FP32 and D <= 13 for HC_FP32_MIXED.
- *   - Every GPU that loads the library holds the array until the process
- *     exits.
- *   - The first call on each device looks up the array's device address
- *     (with that device current); make that first call before any stream
- *     capture.
+ *   - Set-up happens in the first call on each device (in each CUDA
+ *     context): that call loads the library's device code for this entry
+ *     point onto the GPU, which allocates the array there, and looks up the
+ *     array's device address with that device current.  Make this first call
+ *     during set-up -- before any stream capture and before any region in
+ *     which allocation is forbidden; every later call in the same context
+ *     allocates nothing.  The GPU then holds the array until the process
+ *     exits.  After a device reset (cudaDeviceReset, or a primary context
+ *     released and created again) the next call does the set-up again.
  *   - All calls on one device share the array, which keeps whatever the last
  *     call left there; the counters that must start at zero are cleared by
  *     each call itself, on its stream, before its kernels run.  Calls whose work
@@ -252,6 +284,11 @@ hc_status hc_convolve_backward(const void* dz, const void* x, const void* y, voi
  * whether its output (its intermediate, for the grouped form) is a plain
  * device allocation; the groups whose arrays all are store their tiles with
  * bulk copies.
+ * That choice is fixed in the prepared plan: between hc_batched_prepare and
+ * every later hc_batched_launch, each instance's output (and intermediate)
+ * must stay the same kind of memory at the same address -- a buffer freed
+ * and replaced by managed or host-mapped memory at that address needs a new
+ * hc_batched_prepare.
  * hc_batched_launch only resets counters and launches, so it can be captured
  * in a CUDA graph and replayed; every replay recomputes the prepared batch.
  * Device-side waits are bounded: a wait that gives up records HC_ERR_TIMEOUT

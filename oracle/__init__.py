@@ -10,6 +10,8 @@ and marshals numpy arrays.  Functions and the passages they follow:
 
 * :func:`brute_force` -- Algorithm 1 (naive convolution), hypercube case.
 * :func:`points`      -- the definition (Introduction) evaluated at chosen outputs.
+* :func:`carry_free`  -- the carry-free 1D convolution (Discussion), from its
+  definition, for vectors of any length.
 * :func:`convolve`    -- the Methods recurrence (3-way split, base case D = 0;
   ``direct_last_axis=True`` uses the 3-product D = 1 base case instead).
 * :func:`convolve_mixed` -- the same recurrence with binary32 evaluation and
@@ -60,6 +62,7 @@ def _lib():
             vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
             lib.oracle_brute.argtypes = [vp, vp, vp, i, i]
             lib.oracle_points.argtypes = [vp, vp, i, i, vp, sz, vp]
+            lib.oracle_carryfree.argtypes = [vp, vp, vp, sz, i, i]
             lib.oracle_recurrence.argtypes = [vp, vp, vp, i, i, i, i]
             lib.oracle_recurrence_mixed.argtypes = [vp, vp, vp, i]
             lib.oracle_recurrence_inplace.argtypes = [vp, vp, vp, i, i, i]
@@ -122,6 +125,22 @@ def points(x, y, ks) -> np.ndarray:
     if _lib().oracle_points(_ptr(x), _ptr(y), D, code, _ptr(ks), ks.size, _ptr(out)):
         raise RuntimeError("oracle_points failed")
     return out
+
+
+def carry_free(x, y) -> np.ndarray:
+    """Carry-free 1D convolution of two length-N vectors (any N >= 1): the
+    bits of i and j added position by position without carries give the D
+    base-3 digits of the output index, D = (N - 1).bit_length()."""
+    x = np.ascontiguousarray(x).reshape(-1)
+    y = np.ascontiguousarray(y).reshape(-1)
+    if x.dtype != y.dtype or x.dtype not in _DTYPE_CODE or x.size != y.size or x.size < 1:
+        raise ValueError("x and y must be non-empty, of one supported dtype and one length")
+    N = int(x.size)
+    D = (N - 1).bit_length()
+    z = np.empty(3 ** D, dtype=x.dtype)
+    if _lib().oracle_carryfree(_ptr(x), _ptr(y), _ptr(z), N, D, _DTYPE_CODE[x.dtype]):
+        raise RuntimeError("oracle_carryfree failed")
+    return z
 
 
 def convolve(x, y, direct_last_axis: bool = False, threads: int = 1) -> np.ndarray:

@@ -62,6 +62,23 @@ void brute(const T* x, const T* y, T* z, int D) {
     for (size_t j = 0; j < n2; ++j) z[t[i] + t[j]] += x[i] * y[j];
 }
 
+// Carry-free 1D convolution (Discussion): vectors of any length N >= 1 and
+// D = number of bits needed for N - 1.  The bits of i and j are added
+// position by position with no carry; the D resulting digits (each 0, 1 or 2,
+// most significant first) are the base-3 output index.  Straight from that
+// definition, O(N^2); entries no pair reaches stay zero.
+template <class T>
+void carryfree(const T* x, const T* y, T* z, size_t N, int D) {
+  const size_t n3 = pow3(D);
+  for (size_t k = 0; k < n3; ++k) z[k] = T(0);
+  for (size_t i = 0; i < N; ++i)
+    for (size_t j = 0; j < N; ++j) {
+      size_t k = 0;
+      for (int d = D - 1; d >= 0; --d) k = k * 3 + ((i >> d) & 1u) + ((j >> d) & 1u);
+      z[k] += x[i] * y[j];
+    }
+}
+
 // One output of the definition: z[k] = sum of x[i]*y[j] over the 2^{#ones(k)}
 // pairs with i+j = k.  Per axis, digit 0 forces (0,0), digit 2 forces (1,1),
 // digit 1 allows (0,1) and (1,0).  Pairs are visited in increasing i.
@@ -358,6 +375,15 @@ int oracle_brute(const void* x, const void* y, void* z, int D, int dtype) {
     case 0: brute((const u64*)x, (const u64*)y, (u64*)z, D); return 0;
     case 1: brute((const double*)x, (const double*)y, (double*)z, D); return 0;
     case 2: brute((const float*)x, (const float*)y, (float*)z, D); return 0;
+  }
+  return 1;
+}
+
+int oracle_carryfree(const void* x, const void* y, void* z, size_t N, int D, int dtype) {
+  switch (dtype) {
+    case 0: carryfree((const u64*)x, (const u64*)y, (u64*)z, N, D); return 0;
+    case 1: carryfree((const double*)x, (const double*)y, (double*)z, N, D); return 0;
+    case 2: carryfree((const float*)x, (const float*)y, (float*)z, N, D); return 0;
   }
   return 1;
 }

@@ -48,6 +48,8 @@ SIGNATURES = {
     "hc_autotune": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz, _i, _vp, ctypes.c_void_p,
                          ctypes.POINTER(ctypes.c_double)]),
     "hc_convolve_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "hc_carryfree_workspace_size": (_sz, [_sz, _i]),
+    "hc_carryfree": (_i, [_vp, _vp, _vp, _sz, _i, _vp, _sz, _vp]),
     "hc_backward_workspace_size": (_sz, [_i, _i]),
     "hc_convolve_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _sz, _vp]),
     "hc_batched_workspace_size": (_sz, [ctypes.POINTER(hc_instance), _i, _i]),

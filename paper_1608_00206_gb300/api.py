@@ -376,14 +376,30 @@ def convolve_batched(xs, ys, outs=None, *, mixed: bool = False, stream=None, fus
     return b.launch(stream)
 
 
-def carry_free_convolve(x: torch.Tensor, y: torch.Tensor, **kw) -> torch.Tensor:
-    """1D carry-free convolution of two length-N vectors, N = 2^D (paper,
-    Discussion): z[k] = sum of x[i] * y[j] over the pairs whose bitwise,
-    carry-free sum is k, i.e. the digits of k in base 3 are bit_d(i) + bit_d(j).
-    With bit d of the index as axis d (most significant first) this is exactly
-    the hypercube convolution of the flat vectors: z has 3^D entries, entry k
-    read as D base-3 digits.  Example: i = 7 = (1,1,1), j = 5 = (1,0,1) lands
-    in (2,1,2) = 23."""
+def carry_free_convolve(x: torch.Tensor, y: torch.Tensor, *, mixed: bool = False,
+                        workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """1D carry-free convolution of two length-N CUDA vectors (paper,
+    Discussion; hc_carryfree): z[k] = sum of x[i] * y[j] over the pairs whose
+    bitwise, carry-free sum is k, i.e. the base-3 digits of k are
+    bit_d(i) + bit_d(j), with D = ceil(log2 N) digits.  N need not be a power
+    of two: the library zero-pads both vectors to 2^D on the device.  z has
+    3^D entries.  Example: i = 7 = (1,1,1), j = 5 = (1,0,1) lands in
+    (2,1,2) = 23."""
     if x.dim() != 1 or y.dim() != 1:
         raise ValueError("carry-free convolution takes 1D vectors")
-    return convolve(x, y, **kw).reshape(-1)
+    if x.dtype != y.dtype or x.numel() != y.numel() or x.numel() < 1:
+        raise ValueError("x and y must be non-empty and have the same dtype and length")
+    if not (x.is_cuda and y.is_cuda and x.device == y.device):
+        raise ValueError("carry-free convolution takes CUDA tensors on one device")
+    N = x.numel()
+    D = (N - 1).bit_length()
+    code = _code(x.dtype, mixed)
+    x, y = x.contiguous(), y.contiguous()
+    z = torch.empty(3 ** D, dtype=x.dtype, device=x.device)
+    lib = _lib.lib()
+    tuning.ensure_installed(x.device)
+    nbytes = int(lib.hc_carryfree_workspace_size(N, code))
+    ws = _workspace(nbytes, x.device, workspace)
+    check(lib.hc_carryfree(_ptr(x), _ptr(y), _ptr(z), N, code, _ptr(ws), nbytes,
+                           _stream(x.device, stream)), "hc_carryfree")
+    return z

@@ -136,3 +136,54 @@ def test_argument_errors_caught_on_host(L):
     assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, None, ws, size, None) == \
         _lib.HC_ERR_ARG
     assert L.hc_device_status(None, None) == _lib.HC_ERR_ARG
+
+
+# Largest D that hc_convolve_noalloc accepts per dtype, as include/hc.h states
+# it (16 MiB array, built-in chunked schedule).
+NOALLOC_LIMITS = {_lib.HC_INT64: 16, _lib.HC_FP64: 16, _lib.HC_FP32: 17, _lib.HC_FP32_MIXED: 13}
+
+
+@pytest.mark.parametrize("code,limit", sorted(NOALLOC_LIMITS.items()))
+def test_noalloc_limits_per_dtype(L, code, limit):
+    """The documented per-dtype limits of the no-allocation entry point hold:
+    the built-in chunked schedule's workspace fits the fixed array at the
+    limit and not one axis beyond, and a call one axis beyond is refused on
+    the host (fake addresses, no CUDA call)."""
+    cap = 16 << 20
+    builtin = _lib.hc_schedule(_lib.HC_SCHED_CHUNKED, 0, 0, 0, 0)
+    assert L.hc_workspace_size_schedule(limit, code, ctypes.byref(builtin)) <= cap
+    assert L.hc_workspace_size_schedule(limit + 1, code, ctypes.byref(builtin)) > cap
+    D = limit + 1
+    x, y, z = FAKE, FAKE + (1 << 32), FAKE + (1 << 36)
+    assert L.hc_convolve_noalloc(x, y, z, D, code, None) == _lib.HC_ERR_WORKSPACE
+
+
+def test_carryfree_arguments_caught_on_host(L):
+    """hc_carryfree sizes its workspace (padded copies of both vectors plus
+    the plain form's workspace) and rejects bad arguments before any CUDA
+    call."""
+    es = 8
+    for N, D in [(1, 0), (2, 1), (5, 3), (8, 3), (9, 4), (3001, 12)]:
+        nb = L.hc_carryfree_workspace_size(N, _lib.HC_INT64)
+        conv = L.hc_workspace_size(D, _lib.HC_INT64)
+        if N == 1 << D:
+            assert nb == conv
+        else:
+            assert nb >= 2 * (es << D) + conv
+    assert L.hc_carryfree_workspace_size(0, _lib.HC_INT64) == 0
+    assert L.hc_carryfree_workspace_size((1 << _lib.HC_MAX_D) + 1, _lib.HC_INT64) == 0
+    assert L.hc_carryfree_workspace_size(5, 9) == 0
+    x, y, z, ws = FAKE, FAKE + (1 << 20), FAKE + (1 << 24), FAKE + (1 << 30)
+    N = 3001
+    nb = L.hc_carryfree_workspace_size(N, _lib.HC_INT64)
+    cf = L.hc_carryfree
+    assert cf(x, y, z, 0, _lib.HC_INT64, ws, nb, None) == _lib.HC_ERR_ARG
+    assert cf(x, y, z, N, 9, ws, nb, None) == _lib.HC_ERR_DTYPE
+    assert cf(None, y, z, N, _lib.HC_INT64, ws, nb, None) == _lib.HC_ERR_ARG
+    assert cf(x + 8, y, z, N, _lib.HC_INT64, ws, nb, None) == _lib.HC_ERR_ALIGN
+    assert cf(x, y, z, N, _lib.HC_INT64, ws, nb - 1, None) == _lib.HC_ERR_WORKSPACE
+    assert cf(x, y, z, N, _lib.HC_INT64, None, nb, None) == _lib.HC_ERR_ARG
+    assert cf(x, y, z, N, _lib.HC_INT64, ws + 16, nb, None) == _lib.HC_ERR_ALIGN
+    assert cf(x, y, x + 16, N, _lib.HC_INT64, ws, nb, None) == _lib.HC_ERR_ALIAS
+    assert cf(x, y, z, N, _lib.HC_INT64, z, nb, None) == _lib.HC_ERR_ALIAS
+    assert cf(x, y, z, N, _lib.HC_INT64, y - 256, nb, None) == _lib.HC_ERR_ALIAS

@@ -8,7 +8,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
-from paper_1608_00206_gb300 import inputs  # noqa: E402
+from paper_1608_00206_gb300 import _lib, inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -222,15 +222,16 @@ def test_d16_fp64_separable_closed_form(hc):
     assert np.all(np.abs(z - z_closed) <= bound)
 
 
-def test_d20_int64_full_size(hc):
-    """D = 20 int64, values in [-1000, 1000] (the benchmark workload, same
-    launch configuration): 3^20 outputs, 27.9 GB.  Checked on whole slices
-    (prefix digits fixed, the oracle's 16-D recurrence on the matching
-    sub-cube pairs, summed over the pairs of the digit-1 axes), on random
-    single outputs (the definition), and on the sum invariant over all
+@pytest.mark.parametrize("D", [17, 18, 19, 20])
+def test_int64_full_size(hc, D):
+    """D = 17..20 int64, values in [-1000, 1000] (the benchmark workload and
+    its sweep, with the tuned schedule of each D, the launch configuration
+    the benchmark times): 3^D outputs, 27.9 GB at D = 20.  Checked on whole
+    slices (four prefix digits fixed, the oracle's (D-4)-D recurrence on the
+    matching sub-cube pairs, summed over the pairs of the digit-1 axes), on
+    random single outputs (the definition), and on the sum invariant over all
     outputs."""
-    D = 20
-    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2020)
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2000 + D)
     xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
     z = hc.convolve(xt, yt)
     torch.cuda.synchronize()
@@ -239,7 +240,8 @@ def test_d20_int64_full_size(hc):
     # slices with 4 leading digits fixed, by the direct form on those axes:
     # digit 0 -> sub-cube pair (0, 0), 2 -> (1, 1), 1 -> (0, 1) + (1, 0); the
     # slice is the sum over the pairs of the oracle's 16-D recurrence
-    n16 = 3 ** 16
+    r = D - 4  # axes of each slice
+    n16 = 3 ** r
     for digits in [(0, 0, 0, 0), (2, 2, 2, 2), (0, 2, 2, 0), (1, 0, 2, 1)]:
         off_z = sum(d * 3 ** (3 - i) for i, d in enumerate(digits)) * n16
         want = np.zeros(n16, np.int64)
@@ -249,10 +251,10 @@ def test_d20_int64_full_size(hc):
             for q, i in enumerate(ones):
                 bx[i] = (choice >> q) & 1
             by = [d - b for d, b in zip(digits, bx)]
-            sx = sum(b << (3 - i) for i, b in enumerate(bx)) << 16
-            sy = sum(b << (3 - i) for i, b in enumerate(by)) << 16
+            sx = sum(b << (3 - i) for i, b in enumerate(bx)) << r
+            sy = sum(b << (3 - i) for i, b in enumerate(by)) << r
             with np.errstate(over="ignore"):
-                want += oracle.convolve(x[sx:sx + (1 << 16)], y[sy:sy + (1 << 16)], threads=16)
+                want += oracle.convolve(x[sx:sx + (1 << r)], y[sy:sy + (1 << r)], threads=16)
         got = z[off_z:off_z + n16].cpu().numpy()
         assert np.array_equal(got, want), digits
     g = np.random.default_rng(0)
@@ -453,22 +455,59 @@ def test_stream_ordering(hc):
     assert np.array_equal(zc.numpy(), oracle.convolve(x, y))
 
 
-def test_carry_free_1d_convolution(hc):
-    """Discussion section: carry-free 1D convolution is the hypercube
-    convolution of the bit-indexed vectors; 7 (+) 5 lands in (2,1,2) = 23, and
-    a random case matches the definition computed digit by digit."""
+def test_carry_free_1d_convolution(hc, oracle):
+    """Discussion section: carry-free 1D convolution through hc_carryfree;
+    7 (+) 5 lands in (2,1,2) = 23, and random vectors of power-of-two and
+    other lengths match the oracle's definition bit for bit."""
     x = torch.zeros(8, dtype=torch.int64, device=DEV)
     y = torch.zeros(8, dtype=torch.int64, device=DEV)
     x[7], y[5] = 3, 4
     z = hc.carry_free_convolve(x, y).cpu().numpy()
-    assert z[23] == 12 and np.count_nonzero(z) == 1
-    N, D = 1 << 11, 11
+    assert z.size == 27 and z[23] == 12 and np.count_nonzero(z) == 1
     g = np.random.default_rng(5)
-    xs = g.integers(-9, 10, size=N, dtype=np.int64)
-    ys = g.integers(-9, 10, size=N, dtype=np.int64)
-    z = hc.carry_free_convolve(torch.from_numpy(xs).to(DEV), torch.from_numpy(ys).to(DEV))
-    i = np.arange(N)
-    digits = lambda v: sum(((v >> d) & 1) * 3 ** d for d in range(D))  # noqa: E731
-    want = np.zeros(3 ** D, np.int64)
-    np.add.at(want, (digits(i)[:, None] + digits(i)[None, :]).ravel(), np.outer(xs, ys).ravel())
-    assert np.array_equal(z.cpu().numpy(), want)
+    for N in (1, 2, 7, 1 << 11, 1000, 1500, 3001):
+        xs = g.integers(-9, 10, size=N, dtype=np.int64)
+        ys = g.integers(-9, 10, size=N, dtype=np.int64)
+        z = hc.carry_free_convolve(torch.from_numpy(xs).to(DEV), torch.from_numpy(ys).to(DEV))
+        assert np.array_equal(z.cpu().numpy(), oracle.carry_free(xs, ys)), N
+
+
+@pytest.mark.parametrize("code,dt", [(_lib.HC_INT64, np.int64), (_lib.HC_FP64, np.float64),
+                                     (_lib.HC_FP32, np.float32),
+                                     (_lib.HC_FP32_MIXED, np.float32)])
+def test_carry_free_c_abi_every_dtype(oracle, code, dt):
+    """hc_carryfree called through the C ABI on a length that is not a power
+    of two (2^11 < N < 2^12, so the device pads to 2^12): bit for bit the
+    oracle's carry-free definition (int64) or the oracle's recurrence on the
+    zero-padded vectors in the same arithmetic (floats, whose rounding
+    follows the recurrence)."""
+    L = _lib.lib()
+    N = 3001
+    D = (N - 1).bit_length()
+    g = np.random.default_rng(7)
+    if dt is np.int64:
+        x = g.integers(-1000, 1001, size=N, dtype=np.int64)
+        y = g.integers(-1000, 1001, size=N, dtype=np.int64)
+    else:
+        x = g.random(N).astype(dt)
+        y = g.random(N).astype(dt)
+    xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
+    z = torch.empty(3 ** D, dtype=xt.dtype, device=DEV)
+    nb = int(L.hc_carryfree_workspace_size(N, code))
+    assert nb >= 2 * x.itemsize << D
+    ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+    st = torch.cuda.current_stream().cuda_stream
+    _lib.check(L.hc_carryfree(xt.data_ptr(), yt.data_ptr(), z.data_ptr(), N, code, ws.data_ptr(),
+                              nb, st), "hc_carryfree")
+    got = z.cpu().numpy()
+    xp = np.zeros(1 << D, dt)
+    yp = np.zeros(1 << D, dt)
+    xp[:N], yp[:N] = x, y
+    if dt is np.int64:
+        want = oracle.carry_free(x, y)
+    elif code == _lib.HC_FP32_MIXED:
+        want = oracle.convolve_mixed(xp, yp)
+    else:
+        want = oracle.convolve(xp, yp)
+    view = np.uint64 if got.itemsize == 8 else np.uint32
+    assert np.array_equal(got.view(view), want.view(view))

@@ -76,6 +76,58 @@ def test_carry_free_worked_example(oracle):
         assert z[k] == 12 and np.count_nonzero(z) == 1
 
 
+def test_carry_free_oracle_worked_example(oracle):
+    """The 1D carry-free oracle puts x[7] * y[5] at (2,1,2) = 23 (Discussion),
+    not at the carried sum 12."""
+    (D, i, j, digits, k), = _golden("carry_free_example.txt")
+    x = np.zeros(8, np.int64)
+    y = np.zeros(8, np.int64)
+    x[int(i)], y[int(j)] = 3, 4
+    z = oracle.carry_free(x, y)
+    assert z.size == 27 and z[int(k)] == 12 and np.count_nonzero(z) == 1
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 8, 13, 100, 256, 777])
+def test_carry_free_oracle_folds_to_ordinary_convolution(oracle, N):
+    """Applying the carries turns the carry-free convolution back into the
+    ordinary one: summing z[k] over the outputs whose base-3 digits, read as
+    base-2 weights, give m yields (x conv y)[m] (numpy's direct 1D
+    convolution), exactly in int64."""
+    g = np.random.default_rng(N)
+    x = g.integers(-50, 51, size=N, dtype=np.int64)
+    y = g.integers(-50, 51, size=N, dtype=np.int64)
+    z = oracle.carry_free(x, y)
+    D = (N - 1).bit_length()
+    assert z.size == 3 ** D
+    k = np.arange(3 ** D)
+    val2 = np.zeros_like(k)
+    for d in range(D):
+        val2 += (k // 3 ** d % 3) << d
+    folded = np.zeros(2 * N - 1 if N > 1 else 1, np.int64)
+    if D == 0:
+        folded[0] = z[0]
+    else:
+        reach = val2 < folded.size
+        assert not np.any(z[~reach])  # no pair of indices < N lands beyond 2N - 2
+        np.add.at(folded, val2[reach], z[reach])
+    assert np.array_equal(folded, np.convolve(x, y))
+
+
+@pytest.mark.parametrize("N", [2, 8, 64, 3, 6, 45, 200])
+def test_carry_free_oracle_is_padded_hypercube_convolution(oracle, N):
+    """For N = 2^D the carry-free convolution is Algorithm 1 on the vectors as
+    hypercubes; otherwise on the vectors zero-padded to 2^D (float64 too)."""
+    g = np.random.default_rng(100 + N)
+    D = (N - 1).bit_length()
+    for dt in (np.int64, np.float64):
+        x = g.integers(-9, 10, size=N).astype(dt)
+        y = g.integers(-9, 10, size=N).astype(dt)
+        xp = np.zeros(1 << D, dt)
+        yp = np.zeros(1 << D, dt)
+        xp[:N], yp[:N] = x, y
+        assert np.array_equal(oracle.carry_free(x, y), oracle.brute_force(xp, yp))
+
+
 @pytest.mark.parametrize("D", [1, 4, 9])
 def test_delta_inputs(oracle, D):
     """x = e_i, y = e_j gives z = e_{t(i)+t(j)} (single product, no carries)."""

@@ -5,7 +5,8 @@ application forbids it after set-up).  It works in a fixed array inside the
 library instead of a caller workspace.  Its output must equal hc_convolve's
 (bit for bit, the tolerance used throughout these tests) on two calls in a
 row, the second of which finds the first call's leftovers in the shared
-array.  This file is collected last on purpose."""
+array; the first call of each pair is also checked against the CPU oracle.
+This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -57,8 +58,8 @@ CASES = [
 
 
 @pytest.mark.parametrize("code,tdtype,D1,D2", CASES)
-def test_no_alloc_matches_hc_convolve_on_two_calls_in_a_row(L, code, tdtype, D1, D2):
-    outs = []
+def test_no_alloc_matches_hc_convolve_on_two_calls_in_a_row(L, oracle, code, tdtype, D1, D2):
+    outs, hosts = [], []
     for call, D in enumerate((D1, D2)):
         if tdtype == torch.int64:
             x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=10 * D + call)
@@ -70,12 +71,19 @@ def test_no_alloc_matches_hc_convolve_on_two_calls_in_a_row(L, code, tdtype, D1,
         yt = torch.from_numpy(y).to(DEV)
         outs.append((_no_alloc(L, xt, yt, D, code, tdtype),
                      _with_workspace(L, xt, yt, D, code, tdtype)))
+        hosts.append((x, y))
     torch.cuda.synchronize()
     for got, want in outs:
         g = got.cpu().numpy()
         w = want.cpu().numpy()
         view = np.uint64 if g.itemsize == 8 else np.uint32
         assert np.array_equal(g.view(view), w.view(view))
+    # the first call against the oracle in the same arithmetic
+    x, y = hosts[0]
+    ref = oracle.convolve_mixed(x, y) if code == _lib.HC_FP32_MIXED else oracle.convolve(x, y)
+    g = outs[0][0].cpu().numpy()
+    view = np.uint64 if g.itemsize == 8 else np.uint32
+    assert np.array_equal(g.view(view), ref.view(view))
 
 
 def test_no_alloc_refuses_problems_beyond_its_array(L):
