@@ -285,7 +285,7 @@ class Workload:
                 "d16_mixed": 3}[self.name]
         cmax = 9 if code == 2 else 8
         if self.sched:
-            kind = 2 if "m" in self.sched else 1
+            kind = (3 if self.sched.get("bulk") else 2) if "m" in self.sched else 1
             c, k = self.sched.get("c", 0), self.sched.get("m", self.sched.get("kmax", 0))
         else:
             s = _lib.hc_schedule()
@@ -296,7 +296,7 @@ class Workload:
             return kind, C, 0, self.D - C, self.D - C
         m = min(self.D - C, k or 6)
         ap = self.D - C - m
-        return kind, C, m, ap, ap + max(m - 3, 0)
+        return kind, C, m, ap, ap + (m if kind == 3 else max(m - 3, 0))
 
     # per-kernel algorithmic bytes (or FP64 operations) per launch
     def kernel_alg(self, kname, launches_per_step):
@@ -305,7 +305,7 @@ class Workload:
             return self._batched_bytes(kname) / max(launches_per_step, 1), "hbm"
         s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64") else 4
         sw = 8 if self.name == "d16_mixed" else s
-        if kname == "chunk":
+        if kname in ("chunk", "slab"):
             kind, C, m, ap, ev = self.schedule_geometry()
             if self.name == "d16_fp64":
                 tile = 2 * (3 ** C - 2 ** C) + 3 ** C + 2 * C * 3 ** (C - 1)
@@ -820,7 +820,7 @@ def main():
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
-                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked) "
+                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked|bulk) "
                          "instead of the tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
     if args.D is not None and args.workload not in SINGLE + ("fwdbwd",):
@@ -856,12 +856,14 @@ def main():
         if args.workload not in SINGLE:
             ap.error("--schedule applies to single-instance workloads only")
         kind, c, k, cols, *outer = args.schedule.split(":")
+        if kind not in ("passes", "chunked", "bulk"):
+            ap.error("schedule kind is passes, chunked or bulk")
         wl.sched = {"c": int(c), "cols": int(cols),
-                    ("m" if kind == "chunked" else "kmax"): int(k)}
+                    ("kmax" if kind == "passes" else "m"): int(k)}
+        if kind == "bulk":
+            wl.sched["bulk"] = True
         if outer:
             wl.sched["cols_outer"] = int(outer[0])
-        if kind not in ("passes", "chunked"):
-            ap.error("schedule kind is passes or chunked")
         nb = wl.hc.workspace_size(wl.D, wl.z.dtype, wl.mixed, **wl.sched)
         wl.ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
     if args.workload == "d10_int64":

@@ -25,6 +25,17 @@
  *   HC_FP32_MIXED float32 in and out; evaluation (sums) and products in
  *                 float32, the cancelling interpolation (t - z[0]) - z[2] in
  *                 float-float (error-free two-sum), one rounding at the end.
+ *   HC_FP32_FF    float32 in and out; every value of the recurrence in
+ *                 float-float: evaluation by two-sum, products by the FMA
+ *                 two-product (the exact error of the binary32 product)
+ *                 plus the cross terms, interpolation by two-sum; one
+ *                 rounding to float32 at the end.  On integer-valued inputs
+ *                 whose intermediates stay within float-float's 48 bits this
+ *                 is the exact result rounded once.  Plain and
+ *                 differentiation-free: hc_convolve, its schedules,
+ *                 hc_convolve_out (w NULL), hc_convolve_noalloc and
+ *                 hc_carryfree take it; the batched and differentiation
+ *                 forms return HC_ERR_DTYPE.
  *   For every floating-point dtype the library applies the per-axis
  *   operations in the recurrence's own order (evaluation axis 1 first,
  *   interpolation axis D first) with no fused multiply-add, so results are
@@ -68,7 +79,8 @@ typedef enum {
   HC_INT64 = 0,
   HC_FP64 = 1,
   HC_FP32 = 2,
-  HC_FP32_MIXED = 3
+  HC_FP32_MIXED = 3,
+  HC_FP32_FF = 4
 } hc_dtype;
 
 typedef enum {
@@ -121,6 +133,16 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  *                      (tiles of c axes, then the k middle axes interpolated
  *                      while the chunk is in L2); the D - c - k outer axes go
  *                      through whole-array passes.  D <= c + k: one launch.
+ *   HC_SCHED_CHUNKED_BULK : CHUNKED with every middle axis evaluated by the
+ *                      whole-array passes (workspace as for PASSES with c + k
+ *                      tile axes), so that the persistent launch reads plain
+ *                      rows; each tile leaves shared memory in one bulk (TMA
+ *                      engine) copy that L2 keeps (evict_last priority) until
+ *                      the chunk's middle axes are interpolated, and finished
+ *                      columns are stored with evict_first priority.  An
+ *                      intermediate in managed or host-mapped memory, or c
+ *                      other than 7 or 8, runs the CHUNKED kernel on the
+ *                      same plan (same bits).
  *   HC_SCHED_DEFAULT : the per-(D, dtype) default (built in: CHUNKED with
  *                      default sizes; replaced by hc_set_default_schedule,
  *                      typically with hc_autotune's winner).
@@ -136,6 +158,7 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
 #define HC_SCHED_DEFAULT 0
 #define HC_SCHED_PASSES 1
 #define HC_SCHED_CHUNKED 2
+#define HC_SCHED_CHUNKED_BULK 3
 
 typedef struct {
   int kind;
@@ -229,7 +252,8 @@ hc_status hc_carryfree(const void* x, const void* y, void* z, size_t N, hc_dtype
  *   - It always uses the built-in chunked schedule (whatever default schedule
  *     is installed).  Limit: a problem whose workspace for that schedule
  *     exceeds the array is refused with HC_ERR_WORKSPACE.  With 16 MiB that allows D <= 16 for HC_INT64
- *     and HC_FP64, D <= 17 for HC_FP32 and D <= 13 for HC_FP32_MIXED.
+ *     and HC_FP64, D <= 17 for HC_FP32 and D <= 13 for HC_FP32_MIXED and
+ *     HC_FP32_FF.
  *   - Set-up happens in the first call on each device (in each CUDA
  *     context): that call loads the library's device code for this entry
  *     point onto the GPU, which allocates the array there, and looks up the

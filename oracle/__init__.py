@@ -16,6 +16,9 @@ and marshals numpy arrays.  Functions and the passages they follow:
   ``direct_last_axis=True`` uses the 3-product D = 1 base case instead).
 * :func:`convolve_mixed` -- the same recurrence with binary32 evaluation and
   products and float-float interpolation.
+* :func:`convolve_ff` -- the same recurrence with every value in float-float
+  (two-sum evaluation, FMA two-product, two-sum interpolation), binary32 in
+  and out.
 * :func:`adjoint`, :func:`adjoint_brute` -- gradient of the convolution with
   respect to x and y (transpose of the recurrence; brute-force correlation).
 * :func:`zabs` -- magnitude companion for the forward-error bound
@@ -65,6 +68,7 @@ def _lib():
             lib.oracle_carryfree.argtypes = [vp, vp, vp, sz, i, i]
             lib.oracle_recurrence.argtypes = [vp, vp, vp, i, i, i, i]
             lib.oracle_recurrence_mixed.argtypes = [vp, vp, vp, i]
+            lib.oracle_recurrence_ff.argtypes = [vp, vp, vp, i]
             lib.oracle_recurrence_inplace.argtypes = [vp, vp, vp, i, i, i]
             lib.oracle_adjoint.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_adjoint_brute.argtypes = [vp, vp, vp, vp, vp, i, i]
@@ -177,6 +181,17 @@ def convolve_mixed(x, y) -> np.ndarray:
     D = dim_of(x)
     z = np.empty(3 ** D, dtype=np.float32)
     _lib().oracle_recurrence_mixed(_ptr(x), _ptr(y), _ptr(z), D)
+    return z
+
+
+def convolve_ff(x, y) -> np.ndarray:
+    """Float-float evaluation, products (FMA two-product) and interpolation,
+    binary32 in and out: one rounding at the end."""
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
+    D = dim_of(x)
+    z = np.empty(3 ** D, dtype=np.float32)
+    _lib().oracle_recurrence_ff(_ptr(x), _ptr(y), _ptr(z), D)
     return z
 
 

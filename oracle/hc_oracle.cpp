@@ -275,6 +275,59 @@ void rec_mixed(const float* x, const float* y, ff* z, int D, float* scratch) {
 }
 
 // ---------------------------------------------------------------------------
+// Float-float form: every value of the recurrence -- the inputs' sums
+// (evaluation), the products and the interpolation -- is a float-float pair
+// (h, l) of binary32 values, rounded to binary32 once at the end.  The
+// operations, each from its published error-free building blocks:
+//   add(a, b): (s, e) = two_sum(a.h, b.h);  e = e + (a.l + b.l);
+//              (h, l) = quick_two_sum(s, e)
+//   sub(a, b): as add with b negated (ff_sub above)
+//   mul(a, b): p = a.h * b.h;  e = fma(a.h, b.h, -p)   (the exact error of the
+//              binary32 product: TwoProduct with a fused multiply-add, Ogita,
+//              Rump and Oishi 2005);  e = e + (a.h * b.l + a.l * b.h);
+//              (h, l) = quick_two_sum(p, e)
+// Inputs enter as (x, 0).  Same recursion and operation order as rec().
+inline ff ff_add(ff a, ff b) {
+  float s = a.h + b.h;
+  float v = s - a.h;
+  float e = (a.h - (s - v)) + (b.h - v);
+  e = e + (a.l + b.l);
+  float h = s + e;
+  float l = e - (h - s);
+  return ff{h, l};
+}
+
+inline ff ff_mul(ff a, ff b) {
+  float p = a.h * b.h;
+  float e = std::fma(a.h, b.h, -p);
+  float c = a.h * b.l;
+  float d = a.l * b.h;
+  e = e + (c + d);
+  float h = p + e;
+  float l = e - (h - p);
+  return ff{h, l};
+}
+
+void rec_ff(const ff* x, const ff* y, ff* z, int D, ff* scratch) {
+  if (D == 0) {
+    z[0] = ff_mul(x[0], y[0]);
+    return;
+  }
+  const size_t h = (size_t)1 << (D - 1);
+  const size_t n = pow3(D - 1);
+  rec_ff(x, y, z, D - 1, scratch);
+  rec_ff(x + h, y + h, z + 2 * n, D - 1, scratch);
+  ff* xs = scratch;
+  ff* ys = scratch + h;
+  for (size_t k = 0; k < h; ++k) {
+    xs[k] = ff_add(x[k], x[h + k]);
+    ys[k] = ff_add(y[k], y[h + k]);
+  }
+  rec_ff(xs, ys, z + n, D - 1, scratch + 2 * h);
+  for (size_t k = 0; k < n; ++k) z[n + k] = ff_sub(ff_sub(z[n + k], z[k]), z[2 * n + k]);
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint (differentiation form).  For z = x*y and an upstream gradient g =
 // dL/dz, dL/dx[i] = sum_j g[i+j] * y[j] (a correlation).  Splitting axis 1 as
 // in the Methods section gives four correlations of dimension D-1,
@@ -428,6 +481,19 @@ int oracle_recurrence_mixed(const float* x, const float* y, float* z, int D) {
   std::vector<ff> w(pow3(D));
   std::vector<float> scratch(((size_t)2 << D) + 2);
   rec_mixed(x, y, w.data(), D, scratch.data());
+  for (size_t k = 0; k < w.size(); ++k) z[k] = w[k].h + w[k].l;
+  return 0;
+}
+
+int oracle_recurrence_ff(const float* x, const float* y, float* z, int D) {
+  const size_t n2 = (size_t)1 << D;
+  std::vector<ff> xf(n2), yf(n2), w(pow3(D));
+  for (size_t i = 0; i < n2; ++i) {
+    xf[i] = ff{x[i], 0.0f};
+    yf[i] = ff{y[i], 0.0f};
+  }
+  std::vector<ff> scratch(((size_t)2 << D) + 2);
+  rec_ff(xf.data(), yf.data(), w.data(), D, scratch.data());
   for (size_t k = 0; k < w.size(); ++k) z[k] = w[k].h + w[k].l;
   return 0;
 }

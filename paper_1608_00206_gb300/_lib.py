@@ -10,7 +10,7 @@ import threading
 _PKG = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_PKG, "libhc.so")
 
-HC_INT64, HC_FP64, HC_FP32, HC_FP32_MIXED = 0, 1, 2, 3
+HC_INT64, HC_FP64, HC_FP32, HC_FP32_MIXED, HC_FP32_FF = 0, 1, 2, 3, 4
 HC_OK, HC_ERR_ARG, HC_ERR_DTYPE, HC_ERR_ALIGN, HC_ERR_ALIAS = 0, 1, 2, 3, 4
 HC_ERR_WORKSPACE, HC_ERR_CUDA, HC_ERR_TIMEOUT = 5, 6, 7
 HC_MAX_D = 24
@@ -19,7 +19,7 @@ HC_MAX_D = 24
 _vp, _i, _sz, _cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_char_p
 
 
-HC_SCHED_DEFAULT, HC_SCHED_PASSES, HC_SCHED_CHUNKED = 0, 1, 2
+HC_SCHED_DEFAULT, HC_SCHED_PASSES, HC_SCHED_CHUNKED, HC_SCHED_CHUNKED_BULK = 0, 1, 2, 3
 
 
 class hc_schedule(ctypes.Structure):

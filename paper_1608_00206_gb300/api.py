@@ -25,12 +25,19 @@ def dim_of(t: torch.Tensor) -> int:
     return D
 
 
-def _code(dtype: torch.dtype, mixed: bool) -> int:
+def _code(dtype: torch.dtype, mixed) -> int:
+    """Library dtype code.  mixed: False (the tensor's own arithmetic), True
+    (float32 evaluation and products, float-float interpolation) or "ff"
+    (every value in float-float); the last two take float32 tensors."""
     if dtype not in _DT:
         raise TypeError(f"unsupported dtype {dtype}; use int64, float64 or float32")
     if mixed:
         if dtype != torch.float32:
             raise TypeError("mixed precision takes float32 inputs")
+        if mixed == "ff":
+            return _lib.HC_FP32_FF
+        if mixed is not True:
+            raise ValueError(f"mixed is False, True or 'ff'; got {mixed!r}")
         return _lib.HC_FP32_MIXED
     return _DT[dtype]
 
@@ -48,12 +55,15 @@ def _out_shape(x: torch.Tensor, D: int):
     return (3,) * D if (x.dim() == D and all(s == 2 for s in x.shape) and D > 0) else (3 ** D,)
 
 
-def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: int = 0):
+def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: int = 0,
+              bulk: bool = False):
     """None for the default schedule; else an hc_schedule: m > 0 selects the
-    chunked schedule (c tile axes, m middle axes), otherwise c or kmax select
-    the whole-array-pass schedule; cols alone keeps the default kind."""
+    chunked schedule (c tile axes, m middle axes; bulk=True its chunked-bulk
+    variant), otherwise c or kmax select the whole-array-pass schedule; cols
+    alone keeps the default kind."""
     if m:
-        return _lib.hc_schedule(_lib.HC_SCHED_CHUNKED, c, m, cols, cols_outer)
+        kind = _lib.HC_SCHED_CHUNKED_BULK if bulk else _lib.HC_SCHED_CHUNKED
+        return _lib.hc_schedule(kind, c, m, cols, cols_outer)
     if c or kmax:
         return _lib.hc_schedule(_lib.HC_SCHED_PASSES, c, kmax, cols, cols_outer)
     if cols or cols_outer:
@@ -63,9 +73,9 @@ def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: 
 
 def workspace_size(D: int, dtype: torch.dtype = torch.float32, mixed: bool = False,
                    c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0,
-                   cols_outer: int = 0) -> int:
+                   cols_outer: int = 0, bulk: bool = False) -> int:
     code = _code(dtype, mixed)
-    s = _schedule(c, kmax, m, cols, cols_outer)
+    s = _schedule(c, kmax, m, cols, cols_outer, bulk)
     if s is None:
         # the default schedule is the tuned one once the table is installed
         if torch.cuda.is_available():
@@ -116,12 +126,17 @@ _DIRECT_HOST_BYTES = 8 << 30
 def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, *,
              mixed: bool = False, workspace: torch.Tensor | None = None, stream=None,
              c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0,
-             cols_outer: int = 0) -> torch.Tensor:
+             cols_outer: int = 0, bulk: bool = False) -> torch.Tensor:
     """z = x * y over {0,1,2}^D.
+
+    mixed: False (the inputs' own arithmetic), True (float32 evaluation and
+    products, float-float interpolation) or "ff" (every value in
+    float-float, one rounding at the end); the last two take float32.
 
     CUDA tensors: runs on their device and the current (or given) stream,
     asynchronously.  Schedules: default (hc_convolve); m > 0 selects the
-    chunked schedule with m middle axes and c tile axes; otherwise c or kmax
+    chunked schedule with m middle axes and c tile axes (bulk=True: the
+    chunked-bulk variant); otherwise c or kmax
     select the whole-array-pass schedule; cols sets the interpolation tile
     width (cols_outer: that of the pass over the outermost axes).  CPU
     tensors (the end-to-end path): x and y are copied to
@@ -135,7 +150,7 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
         raise ValueError("x and y must have the same dtype and size")
     D = dim_of(x)
     code = _code(x.dtype, mixed)
-    sched = _schedule(c, kmax, m, cols, cols_outer)
+    sched = _schedule(c, kmax, m, cols, cols_outer, bulk)
     if x.is_cuda:
         if not y.is_cuda or y.device != x.device:
             raise ValueError("x and y must be on the same CUDA device")

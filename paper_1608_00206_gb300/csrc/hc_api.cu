@@ -46,7 +46,30 @@ size_t elem_size(hc_dtype dt) {
     case HC_INT64:
     case HC_FP64: return 8;
     case HC_FP32:
+    case HC_FP32_MIXED:
+    case HC_FP32_FF: return 4;
+  }
+  return 0;
+}
+
+size_t in_size(hc_dtype dt) {
+  switch (dt) {
+    case HC_INT64:
+    case HC_FP64:
+    case HC_FP32_FF: return 8;
+    case HC_FP32:
     case HC_FP32_MIXED: return 4;
+  }
+  return 0;
+}
+
+size_t w_size(hc_dtype dt) {
+  switch (dt) {
+    case HC_FP32: return 4;
+    case HC_INT64:
+    case HC_FP64:
+    case HC_FP32_MIXED:
+    case HC_FP32_FF: return 8;
   }
   return 0;
 }

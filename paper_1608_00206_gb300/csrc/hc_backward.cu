@@ -694,7 +694,7 @@ static cudaError_t run_backward(const BwdPlan& p, const void* dz, const void* x,
 }  // namespace hc
 
 extern "C" size_t hc_backward_workspace_size(int D, hc_dtype dtype) {
-  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0 || dtype == HC_FP32_MIXED) return 0;
+  if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0 || hc::wide_intermediate(dtype)) return 0;
   return hc::make_bwd_plan(D, dtype).ws_bytes;
 }
 
@@ -704,7 +704,7 @@ extern "C" hc_status hc_convolve_backward(const void* dz, const void* x, const v
   using namespace hc;
   if (D < 0 || D > HC_MAX_D) return HC_ERR_ARG;
   const size_t es = elem_size(dtype);
-  if (es == 0 || dtype == HC_FP32_MIXED) return HC_ERR_DTYPE;
+  if (es == 0 || hc::wide_intermediate(dtype)) return HC_ERR_DTYPE;
   if (!dz || !x || !y || (!dx && !dy)) return HC_ERR_ARG;
   if (!aligned(dz, 16) || !aligned(x, 16) || !aligned(y, 16) || (dx && !aligned(dx, 16)) ||
       (dy && !aligned(dy, 16)))

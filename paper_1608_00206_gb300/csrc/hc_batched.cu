@@ -231,7 +231,7 @@ static hc_status build_batch(const hc_instance* inst, int n, hc_dtype dt, int fu
                              std::vector<std::vector<GroupPtrs>>* gtabs, void* workspace) {
   if (n < 0 || (n > 0 && !inst)) return HC_ERR_ARG;
   const size_t es = elem_size(dt);
-  if (es == 0) return HC_ERR_DTYPE;
+  if (es == 0 || dt == HC_FP32_FF) return HC_ERR_DTYPE;  // FF: plain form only
   const int cmax = batch_cmax(dt);
   const size_t wsz = (dt == HC_FP32_MIXED) ? 8 : es;
   const bool mixed = dt == HC_FP32_MIXED;

@@ -7,7 +7,14 @@
 #include "hc_kernels.cuh"
 #include "hc_persist.cuh"
 #include "hc_profile.cuh"
+#include "hc_slab.cuh"
 #include "hc_tile.cuh"
+
+// L2 priorities in the chunk engine (tiles kept, finished columns streamed
+// out); -DHC_CHUNK_L2HINT=0 builds the engine with plain accesses.
+#ifndef HC_CHUNK_L2HINT
+#define HC_CHUNK_L2HINT 1
+#endif
 
 namespace hc {
 
@@ -15,7 +22,8 @@ template <class M, int C, bool FIN>
 __global__ void __launch_bounds__(256, (sizeof(typename M::W) == 4 ? 3 : 2)) chunk_kernel(UniformUnits uu, long long total,
                                                     unsigned long long* counters, WsHeader* hdr) {
   extern __shared__ __align__(16) unsigned char smem[];
-  persistent_loop<M, C, true, FIN>(nullptr, nullptr, uu, total, counters, hdr, smem);
+  persistent_loop<M, C, true, FIN, HC_CHUNK_L2HINT != 0>(nullptr, nullptr, uu, total, counters,
+                                                           hdr, smem);
 }
 
 template <class M, int C, bool FIN>
@@ -48,6 +56,51 @@ static cudaError_t launch_chunk(const ChunkPlan& p, const UniformUnits& uu,
       if constexpr (sizeof(typename M::W) == 4) return launch_chunk_c<M, 9, FIN>(p, uu, ctr, hdr, st);
       return cudaErrorInvalidValue;
   }
+  return cudaErrorInvalidValue;
+}
+
+// The slab kernel of the chunked-bulk schedule, for a compile-time tile C and
+// m middle axes.
+template <class M, int C, int MM, bool FIN>
+static cudaError_t launch_slab_cm(const ChunkPlan& p, const SlabArgs& a0, cudaStream_t st) {
+  auto k = slab_kernel<M, C, MM, FIN>;
+  ProfileScope prof(st, "slab");
+  const size_t smem = SlabSmem<M, C, MM>::bytes;
+  cudaError_t e = prep_kernel(k, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = grid_for(k, 256, smem, p.total);
+  SlabArgs a = a0;
+  a.uu.lag = grid < p.n_tiles ? grid : p.n_tiles;  // one wave of CTAs (see uniform_ticket)
+  k<<<grid, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class M, int C, bool FIN>
+static cudaError_t launch_slab_c(const ChunkPlan& p, const SlabArgs& a, cudaStream_t st) {
+  switch (p.m) {
+    case 1: return launch_slab_cm<M, C, 1, FIN>(p, a, st);
+    case 2: return launch_slab_cm<M, C, 2, FIN>(p, a, st);
+    case 3: return launch_slab_cm<M, C, 3, FIN>(p, a, st);
+    case 4: return launch_slab_cm<M, C, 4, FIN>(p, a, st);
+    case 5: return launch_slab_cm<M, C, 5, FIN>(p, a, st);
+    case 6: return launch_slab_cm<M, C, 6, FIN>(p, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Tile sizes the slab kernel is built for: C = 7 and 8, whose two W tiles
+// and rows fit one CTA's shared memory for every dtype (a 9-axis float32
+// tile does not: the chunked-bulk plan then runs on the generic engine).
+template <class M>
+static bool slab_supported(int C, int m) {
+  return m >= 1 && m <= 6 && (C == 7 || C == 8);
+}
+
+template <class M, bool FIN>
+static cudaError_t launch_slab(const ChunkPlan& p, const SlabArgs& a, cudaStream_t st) {
+  static_assert(SlabSmem<M, 8, 6>::bytes <= 227 * 1024, "slab tiles fit one CTA");
+  if (p.C == 8) return launch_slab_c<M, 8, FIN>(p, a, st);
+  if (p.C == 7) return launch_slab_c<M, 7, FIN>(p, a, st);
   return cudaErrorInvalidValue;
 }
 
@@ -97,10 +150,27 @@ static cudaError_t chunk_forward_m(const ChunkPlan& p, const void* x, const void
   uu.cpt = p.cpt;
   uu.need = p.n_tiles;
   unsigned long long* ctr = (unsigned long long*)(ws + p.off_ctr);
-  if (fin)
+  // The chunked-bulk schedule (every middle axis evaluated above) runs the
+  // slab kernel where its bulk tile copies apply: a tile size it is built
+  // for and an intermediate in a plain device allocation.  Otherwise the
+  // generic engine runs the same plan (its on-the-fly evaluation then has no
+  // axis left to evaluate), with the same bits.
+  if (p.bulk && p.m_pre == p.m && slab_supported<M>(p.C, p.m) && is_device_allocation(wbuf)) {
+    SlabArgs a;
+    a.x = X;
+    a.y = Y;
+    a.w = wbuf;
+    a.z = fin ? z : (void*)wbuf;
+    a.ctr = ctr;
+    a.hdr = (WsHeader*)ws;
+    a.uu = uu;
+    a.total = p.total;
+    e = fin ? launch_slab<M, true>(p, a, st) : launch_slab<M, false>(p, a, st);
+  } else if (fin) {
     e = launch_chunk<M, true>(p, uu, ctr, (WsHeader*)ws, st);
-  else
+  } else {
     e = launch_chunk<M, false>(p, uu, ctr, (WsHeader*)ws, st);
+  }
   if (e != cudaSuccess) return e;
   // whole-array interpolation of the a' outer axes, innermost pass first
   for (int i = 0; i < p.n_interp; ++i) {

@@ -63,6 +63,33 @@ __device__ __forceinline__ ffv ff_sub(ffv a, ffv b) {
   return ffv{h, l};
 }
 
+// a + b in float-float: Knuth's two-sum on the high parts, the low parts
+// added to the error, then Dekker's quick-two-sum (ff_sub with b negated).
+__device__ __forceinline__ ffv ff_add(ffv a, ffv b) {
+  float s = __fadd_rn(a.h, b.h);
+  float v = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  float h = __fadd_rn(s, e);
+  float l = __fsub_rn(e, __fsub_rn(h, s));
+  return ffv{h, l};
+}
+
+// a * b in float-float: the binary32 product of the high parts and its exact
+// error from one fused multiply-add (the FMA two-product of Ogita, Rump and
+// Oishi), the cross terms added to the error, then quick-two-sum.  The FMA
+// here is deliberate: its result is the exact residual a.h * b.h - p.
+__device__ __forceinline__ ffv ff_mul(ffv a, ffv b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  const float c = __fmul_rn(a.h, b.l);
+  const float d = __fmul_rn(a.l, b.h);
+  e = __fadd_rn(e, __fadd_rn(c, d));
+  const float h = __fadd_rn(p, e);
+  const float l = __fsub_rn(e, __fsub_rn(h, p));
+  return ffv{h, l};
+}
+
 // Arithmetic modes.  In: element of x and y (and of the evaluated operands);
 // W: element of products and interpolation intermediates; Out: element of z.
 struct ModeI64 {  // Z/2^64
@@ -125,6 +152,23 @@ struct ModeMixed {
   static constexpr hc_dtype kDtype = HC_FP32_MIXED;
   static __device__ __forceinline__ In add(In a, In b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ W mul(In a, In b) { return ffv{__fmul_rn(a, b), 0.0f}; }
+  static __device__ __forceinline__ W mid(W p0, W p1, W p2) {
+    return ff_sub(ff_sub(p1, p0), p2);
+  }
+  static __device__ __forceinline__ Out out(W w) { return __fadd_rn(w.h, w.l); }
+  static __device__ __forceinline__ W win(Out v) { return ffv{v, 0.0f}; }
+};
+
+// Every value in float-float: evaluation (ff_add), products (ff_mul, exact
+// high product) and interpolation (ff_sub); binary32 in and out.  The
+// binary32 inputs are widened to (x, 0) pairs before the first pass.
+struct ModeFF {
+  typedef ffv In;
+  typedef ffv W;
+  typedef float Out;
+  static constexpr hc_dtype kDtype = HC_FP32_FF;
+  static __device__ __forceinline__ In add(In a, In b) { return ff_add(a, b); }
+  static __device__ __forceinline__ W mul(In a, In b) { return ff_mul(a, b); }
   static __device__ __forceinline__ W mid(W p0, W p1, W p2) {
     return ff_sub(ff_sub(p1, p0), p2);
   }
@@ -253,6 +297,11 @@ hc_status record_cuda_error(cudaError_t e);  // remembers CUDA's message; HC_OK 
 bool aligned(const void* p, size_t a);
 bool overlaps(const void* a, size_t na, const void* b, size_t nb);
 size_t elem_size(hc_dtype dt);  // bytes of one x/y/z element (0 for unknown)
+size_t in_size(hc_dtype dt);    // bytes of one evaluated-operand element (M::In)
+size_t w_size(hc_dtype dt);     // bytes of one intermediate element (M::W)
+// Whether the 3^D intermediate is of another type than z (float-float
+// intermediates, binary32 output): it then lives in the workspace.
+inline bool wide_intermediate(hc_dtype dt) { return dt == HC_FP32_MIXED || dt == HC_FP32_FF; }
 size_t align_up(size_t v, size_t a);
 
 // Workspace header: the first 256 bytes of every workspace.

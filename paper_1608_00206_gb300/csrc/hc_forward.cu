@@ -77,6 +77,20 @@ __global__ void __launch_bounds__(256) tile_conv_bulk_kernel(const typename M::I
                        [&](long long t) { return out + t * p3(C); }, ntiles, smem);
 }
 
+// HC_FP32_FF: the binary32 inputs as float-float pairs (x, 0), written once
+// before the first pass (blockIdx.y selects the operand).
+__global__ void __launch_bounds__(256) widen_ff_kernel(const float* __restrict__ x,
+                                                       const float* __restrict__ y,
+                                                       ffv* __restrict__ xw, ffv* __restrict__ yw,
+                                                       long long n) {
+  const float* s = blockIdx.y ? y : x;
+  ffv* d = blockIdx.y ? yw : xw;
+#pragma unroll 1
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    d[i] = ffv{s[i], 0.0f};
+}
+
 // D = 0: z[0] = x[0] * y[0].
 template <class M>
 __global__ void scalar_conv_kernel(const typename M::In* x, const typename M::In* y,
@@ -150,8 +164,8 @@ FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req) {
   p.a = D - C;
   int kmax = kmax_req > 0 ? kmax_req : 6;
   if (kmax > 6) kmax = 6;
-  const size_t in_sz = (dt == HC_INT64 || dt == HC_FP64) ? 8 : 4;
-  const size_t w_sz = (dt == HC_FP32) ? 4 : 8;
+  const size_t in_sz = in_size(dt);
+  const size_t w_sz = w_size(dt);
   // K1 passes: groups of <= 3 outer axes, outer first.
   for (int d = 0; d < p.a; d += 3) {
     const int k = (p.a - d) < 3 ? (p.a - d) : 3;
@@ -192,7 +206,7 @@ FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req) {
   p.off_ty = off;
   off = align_up(off + tmax * in_sz, 256);
   p.off_w = off;
-  if (dt == HC_FP32_MIXED && p.a > 0) off = align_up(off + pow3z(D) * w_sz, 256);
+  if (wide_intermediate(dt) && p.a > 0) off = align_up(off + pow3z(D) * w_sz, 256);
   p.ws_bytes = off;
   return p;
 }
@@ -255,7 +269,7 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
   return cudaSuccess;
 }
 
-ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
+ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req, bool bulk) {
   ChunkPlan p;
   memset(&p, 0, sizeof(p));
   p.D = D;
@@ -267,11 +281,12 @@ ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
   p.C = C;
   p.m = (D - C) < mmax ? (D - C) : mmax;
   p.ap = D - C - p.m;
-  const size_t es = elem_size(dt);
-  const size_t wsz = (dt == HC_FP32 || dt == HC_INT64 || dt == HC_FP64) ? es : 8;
+  const size_t es = in_size(dt);  // evaluated-operand elements
+  const size_t wsz = w_size(dt);
   // The first m - 3 middle axes are evaluated together with the a' outer
   // axes, leaving at most 3 to evaluate on the fly inside the tiles.
-  p.m_pre = p.m > 3 ? p.m - 3 : 0;
+  p.bulk = bulk;
+  p.m_pre = bulk ? p.m : (p.m > 3 ? p.m - 3 : 0);
   const int ev = p.ap + p.m_pre;  // axes evaluated by whole-array passes
   // whole-array evaluation passes (<= 3 axes each, outer first)
   for (int d = 0; d < ev; d += 3) {
@@ -330,7 +345,7 @@ ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req) {
   p.off_yo = take(xo * es);
   p.off_tx = take(tmax * es);
   p.off_ty = take(tmax * es);
-  p.off_w = take((dt == HC_FP32_MIXED && (p.m > 0 || p.ap > 0)) ? pow3z(D) * wsz : 0);
+  p.off_w = take((wide_intermediate(dt) && (p.m > 0 || p.ap > 0)) ? pow3z(D) * wsz : 0);
   p.ws_bytes = off;
   return p;
 }
@@ -342,6 +357,7 @@ cudaError_t chunk_dispatch(const ChunkPlan& p, const void* x, const void* y, voi
     case HC_FP64: return chunk_forward_f64(p, x, y, z, ws, st, w);
     case HC_FP32: return chunk_forward_f32(p, x, y, z, ws, st, w);
     case HC_FP32_MIXED: return chunk_forward_mix(p, x, y, z, ws, st, w);
+    case HC_FP32_FF: return chunk_forward_ff(p, x, y, z, ws, st, w);
   }
   return cudaErrorInvalidValue;
 }
@@ -353,6 +369,7 @@ cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, voi
     case HC_FP64: return run_forward<ModeF64>(p, x, y, z, ws, st, w);
     case HC_FP32: return run_forward<ModeF32>(p, x, y, z, ws, st, w);
     case HC_FP32_MIXED: return run_forward<ModeMixed>(p, x, y, z, ws, st, w);
+    case HC_FP32_FF: return run_forward<ModeFF>(p, x, y, z, ws, st, w);
   }
   return cudaErrorInvalidValue;
 }
@@ -370,7 +387,7 @@ static bool g_has_default[HC_MAX_D + 1][4];
 
 bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
   const int cmax = dtype == HC_FP32 ? 9 : 8;
-  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_CHUNKED) return false;
+  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_CHUNKED_BULK) return false;
   if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
   auto width_ok = [](int w) {
     return w == 0 || w == 8 || w == 16 || w == 32 || w == -16 || w == -32;
@@ -400,16 +417,26 @@ static FwdPlan passes_plan(int D, hc_dtype dt, const hc_schedule& s) {
 }
 
 static ChunkPlan chunked_plan(int D, hc_dtype dt, const hc_schedule& s) {
-  ChunkPlan p = make_chunk_plan(D, dt, s.c, s.k);
+  ChunkPlan p = make_chunk_plan(D, dt, s.c, s.k, s.kind == HC_SCHED_CHUNKED_BULK);
   p.cols = s.cols;
   p.cols_outer = s.cols_outer;
   return p;
 }
 
-size_t schedule_ws(int D, hc_dtype dtype, const hc_schedule& s) {
-  if (D < 0 || D > HC_MAX_D || elem_size(dtype) == 0) return 0;
+// HC_FP32_FF: the widened inputs, two arrays of 2^D float-float pairs after
+// the plan's own workspace.
+static size_t widen_bytes(int D, hc_dtype dtype) {
+  return dtype == HC_FP32_FF ? 2 * align_up(sizeof(ffv) << D, 256) : 0;
+}
+
+static size_t plan_ws(int D, hc_dtype dtype, const hc_schedule& s) {
   if (s.kind == HC_SCHED_PASSES || D == 0) return passes_plan(D, dtype, s).ws_bytes;
   return chunked_plan(D, dtype, s).ws_bytes;
+}
+
+size_t schedule_ws(int D, hc_dtype dtype, const hc_schedule& s) {
+  if (D < 0 || D > HC_MAX_D || elem_size(dtype) == 0) return 0;
+  return plan_ws(D, dtype, s) + widen_bytes(D, dtype);
 }
 
 hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtype dtype,
@@ -438,6 +465,25 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
         (workspace && need > 0 && overlaps(w, nz, workspace, need)))
       return HC_ERR_ALIAS;
   }
+  if (dtype == HC_FP32_FF) {
+    // widen x, y into the workspace's tail; the passes then read pairs
+    unsigned char* tail = (unsigned char*)workspace + plan_ws(D, dtype, s);
+    ffv* xw = (ffv*)tail;
+    ffv* yw = (ffv*)(tail + align_up(sizeof(ffv) << D, 256));
+    const long long n = 1ll << D;
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)device_caps().sms * 8;
+    if (blocks > cap) blocks = cap;
+    {
+      ProfileScope prof(stream, "widen");
+      widen_ff_kernel<<<dim3((unsigned)blocks, 2), 256, 0, stream>>>((const float*)x,
+                                                                    (const float*)y, xw, yw, n);
+    }
+    const hc_status wst = record_cuda_error(cudaGetLastError());
+    if (wst != HC_OK) return wst;
+    x = xw;
+    y = yw;
+  }
   if (s.kind == HC_SCHED_PASSES || D == 0)
     return record_cuda_error(forward_dispatch(passes_plan(D, dtype, s), x, y, z,
                                               (unsigned char*)workspace, stream, w));
@@ -459,6 +505,7 @@ static std::vector<hc_schedule> tune_candidates(int D, hc_dtype dtype) {
       for (int ci = 0; ci < 5; ++ci) {
         v.push_back({HC_SCHED_PASSES, c, k, cols[ci], 0});
         v.push_back({HC_SCHED_CHUNKED, c, k, cols[ci], 0});
+        v.push_back({HC_SCHED_CHUNKED_BULK, c, k, cols[ci], 0});
       }
   }
   return v;
@@ -491,7 +538,7 @@ extern "C" hc_status hc_convolve_schedule(const void* x, const void* y, void* z,
 extern "C" hc_status hc_convolve_out(const void* x, const void* y, void* w, void* z, int D,
                                      hc_dtype dtype, void* workspace, size_t ws_bytes,
                                      hc_stream_t stream) {
-  if (dtype == HC_FP32_MIXED) {
+  if (hc::wide_intermediate(dtype)) {
     if (w) return HC_ERR_ARG;  // its intermediate lives in the workspace
   } else if (!w) {
     return HC_ERR_ARG;

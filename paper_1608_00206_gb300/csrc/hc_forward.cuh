@@ -43,10 +43,13 @@ struct ChunkPlan {
   size_t ws_bytes;
   int cols;        // columns per whole-array interpolation tile (0 = default)
   int cols_outer;  // the same for the pass over the outermost axes (0 = cols)
+  bool bulk;       // chunked-bulk: every middle axis pre-evaluated, slab kernel
 };
 
-// c_req: tile axes (0 = default); m_req: middle axes per chunk (0 = default).
-ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req);
+// c_req: tile axes (0 = default); m_req: middle axes per chunk (0 = default);
+// bulk: the chunked-bulk variant (all m middle axes evaluated by the
+// whole-array passes, tiles stored by bulk copies).
+ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req, bool bulk = false);
 
 cudaError_t chunk_forward_i64(const ChunkPlan& p, const void* x, const void* y, void* z,
                               unsigned char* ws, cudaStream_t st, void* w = nullptr);
@@ -56,6 +59,8 @@ cudaError_t chunk_forward_f32(const ChunkPlan& p, const void* x, const void* y, 
                               unsigned char* ws, cudaStream_t st, void* w = nullptr);
 cudaError_t chunk_forward_mix(const ChunkPlan& p, const void* x, const void* y, void* z,
                               unsigned char* ws, cudaStream_t st, void* w = nullptr);
+cudaError_t chunk_forward_ff(const ChunkPlan& p, const void* x, const void* y, void* z,
+                             unsigned char* ws, cudaStream_t st, void* w = nullptr);
 
 // c_req, kmax_req <= 0 select the defaults (largest tile, 6 axes per pass).
 FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);

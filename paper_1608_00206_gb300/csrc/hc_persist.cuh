@@ -176,7 +176,7 @@ __device__ __forceinline__ void tile_any_c(int C, const OtfLoader<M>& ld, void* 
 
 // m <= 3 middle axes: every thread takes whole columns of [c0, c1), no
 // shared memory.
-template <class M, int K, bool FIN>
+template <class M, int K, bool FIN, int SPOL = kPolNone, int LPOL = kPolNone>
 __device__ __forceinline__ void cols_small_k(const typename M::W* src, void* dst, long long c0,
                                              long long c1, long long lo) {
   typedef typename M::W W;
@@ -185,25 +185,26 @@ __device__ __forceinline__ void cols_small_k(const typename M::W* src, void* dst
   for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     W v[p3(K)];
 #pragma unroll
-    for (int j = 0; j < p3(K); ++j) v[j] = ldw<true>(src + j * lo + c);
+    for (int j = 0; j < p3(K); ++j) v[j] = ld_cg_pol<LPOL>(src + j * lo + c);
     interp_pencil<M, K>(v);
     if constexpr (FIN) {
 #pragma unroll
-      for (int j = 0; j < p3(K); ++j) reinterpret_cast<Out*>(dst)[j * lo + c] = M::out(v[j]);
+      for (int j = 0; j < p3(K); ++j)
+        st_pol<SPOL>(reinterpret_cast<Out*>(dst) + j * lo + c, M::out(v[j]));
     } else {
 #pragma unroll
-      for (int j = 0; j < p3(K); ++j) reinterpret_cast<W*>(dst)[j * lo + c] = v[j];
+      for (int j = 0; j < p3(K); ++j) st_pol<SPOL>(reinterpret_cast<W*>(dst) + j * lo + c, v[j]);
     }
   }
 }
 
-template <class M, bool FIN>
+template <class M, bool FIN, int SPOL = kPolNone>
 __device__ __forceinline__ void cols_small(int m, const typename M::W* src, void* dst,
                                            long long c0, long long c1, long long lo) {
   switch (m) {
-    case 1: cols_small_k<M, 1, FIN>(src, dst, c0, c1, lo); break;
-    case 2: cols_small_k<M, 2, FIN>(src, dst, c0, c1, lo); break;
-    case 3: cols_small_k<M, 3, FIN>(src, dst, c0, c1, lo); break;
+    case 1: cols_small_k<M, 1, FIN, SPOL>(src, dst, c0, c1, lo); break;
+    case 2: cols_small_k<M, 2, FIN, SPOL>(src, dst, c0, c1, lo); break;
+    case 3: cols_small_k<M, 3, FIN, SPOL>(src, dst, c0, c1, lo); break;
   }
 }
 
@@ -251,7 +252,11 @@ __device__ __forceinline__ void uniform_ticket(long long t, const UniformUnits& 
 // CT > 0: every unit has C = CT (compile-time tile); CT < 0: per-unit C.
 // UNIFORM: units from `uu`; else (unit, local) = ticket_map[t], unit desc[unit].
 // FIN: column tickets write Out elements to z (float-float -> binary32).
-template <class M, int CT, bool UNIFORM, bool FIN>
+// L2HINT: tiles are stored with L2 priority evict_last (their unit's column
+// tickets read them back from L2) and finished columns with evict_first
+// (nothing in the launch reads them again), so that the units in flight keep
+// their place in L2.
+template <class M, int CT, bool UNIFORM, bool FIN, bool L2HINT = false>
 __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ desc,
                                                 const int2* __restrict__ ticket_map,
                                                 const UniformUnits& uu, long long total,
@@ -347,7 +352,8 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
       } else {
         W* out = (W*)d.w + (long long)loc * (CT > 0 ? p3(CT > 0 ? CT : 1) : pow3i(C));
         if constexpr (CT > 0)
-          tile_body<M, (CT > 0 ? CT : 1), false>(ld, out, smem);
+          tile_body<M, (CT > 0 ? CT : 1), false, OtfLoader<M>, false,
+                    L2HINT ? kPolKeep : kPolNone>(ld, out, smem);
         else
           tile_any_c<M, false>(C, ld, out, smem);
         // release: a barrier (the tile body's last one for tiles of more than
@@ -391,8 +397,9 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
         const long long lo = CT > 0 ? p3(CT > 0 ? CT : 1) : pow3i(C);
         const long long c0 = (local - d.n_tiles) * d.cpt * L;
         const long long c1 = (c0 + (long long)d.cpt * L < lo) ? c0 + (long long)d.cpt * L : lo;
+        constexpr int SP = L2HINT ? kPolStream : kPolNone;
         if (d.m <= 3) {
-          cols_small<M, FIN>(d.m, (const W*)d.w, d.z, c0, c1, lo);
+          cols_small<M, FIN, SP>(d.m, (const W*)d.w, d.z, c0, c1, lo);
         } else {
           const int n = (int)((c1 - c0 + L - 1) / L);
           auto tile = [&](int i, long long& base, long long& l0) {
@@ -400,9 +407,18 @@ __device__ __forceinline__ void persistent_loop(const UnitDesc* __restrict__ des
             base = l0;
           };
           switch (d.m) {
-            case 4: interp_tiles_pipelined<M, 1, 3, L, FIN>((const W*)d.w, d.z, lo, n, tile, smem); break;
-            case 5: interp_tiles_pipelined<M, 2, 3, L, FIN>((const W*)d.w, d.z, lo, n, tile, smem); break;
-            case 6: interp_tiles_pipelined<M, 3, 3, L, FIN>((const W*)d.w, d.z, lo, n, tile, smem); break;
+            case 4:
+              interp_tiles_pipelined<M, 1, 3, L, FIN, decltype(tile), false, NoPtrs, kPolNone, SP>(
+                  (const W*)d.w, d.z, lo, n, tile, smem);
+              break;
+            case 5:
+              interp_tiles_pipelined<M, 2, 3, L, FIN, decltype(tile), false, NoPtrs, kPolNone, SP>(
+                  (const W*)d.w, d.z, lo, n, tile, smem);
+              break;
+            case 6:
+              interp_tiles_pipelined<M, 3, 3, L, FIN, decltype(tile), false, NoPtrs, kPolNone, SP>(
+                  (const W*)d.w, d.z, lo, n, tile, smem);
+              break;
           }
         }
       }

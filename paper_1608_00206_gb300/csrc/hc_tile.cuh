@@ -44,6 +44,86 @@ __device__ __forceinline__ T ldw(const T* p) {
   }
 }
 
+// L2 eviction priority of a global access (createpolicy, .L2::cache_hint).
+// kPolNone: a plain access.  kPolKeep (evict_last): data that other CTAs of
+// the same launch read back soon, e.g. a chunk's tiles before its column
+// tickets; kept in L2 ahead of other lines.  kPolStream (evict_first): data
+// the launch does not touch again, e.g. a chunk's finished columns; the
+// first to leave L2, so they do not push out the lines still in use.
+enum : int { kPolNone = 0, kPolKeep = 1, kPolStream = 2 };
+
+template <int POL>
+__device__ __forceinline__ unsigned long long l2_policy() {
+  unsigned long long p = 0;
+  if constexpr (POL == kPolKeep)
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else if constexpr (POL == kPolStream)
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// *p = v with the L2 priority POL (p: global memory).
+template <int POL, class T>
+__device__ __forceinline__ void st_pol(T* p, const T& v) {
+  if constexpr (POL == kPolNone) {
+    *p = v;
+  } else {
+    static_assert(sizeof(T) == 8 || sizeof(T) == 4, "4- or 8-byte elements");
+    const unsigned long long pol = l2_policy<POL>();
+    if constexpr (sizeof(T) == 8) {
+      unsigned long long b;
+      memcpy(&b, &v, 8);
+      asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(b), "l"(pol)
+                   : "memory");
+    } else {
+      unsigned b;
+      memcpy(&b, &v, 4);
+      asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(b), "l"(pol)
+                   : "memory");
+    }
+  }
+}
+
+// cp.async of 4 or 8 bytes with the L2 priority POL on the global read.
+template <int BYTES, int POL>
+__device__ __forceinline__ void cp_async_pol(void* smem, const void* gmem) {
+  if constexpr (POL == kPolNone) {
+    cp_async<BYTES>(smem, gmem);
+  } else {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const unsigned long long pol = l2_policy<POL>();
+    if constexpr (BYTES == 8)
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s),
+                   "l"(gmem), "l"(pol)
+                   : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;\n" ::"r"(s),
+                   "l"(gmem), "l"(pol)
+                   : "memory");
+  }
+}
+
+// A load through L2 only (as ldw<true>) with the L2 priority POL.
+template <int POL, class T>
+__device__ __forceinline__ T ld_cg_pol(const T* p) {
+  if constexpr (POL == kPolNone) {
+    return ldw<true>(p);
+  } else {
+    const unsigned long long pol = l2_policy<POL>();
+    T r;
+    if constexpr (sizeof(T) == 8) {
+      unsigned long long b;
+      asm volatile("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(b) : "l"(p), "l"(pol));
+      memcpy(&r, &b, 8);
+    } else {
+      unsigned b;
+      asm volatile("ld.global.cg.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(b) : "l"(p), "l"(pol));
+      memcpy(&r, &b, 4);
+    }
+    return r;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K2: the fused tile.  C inner axes, split into G = ceil(C/3) groups of at
 // most 3 axes (the outermost group takes the remainder).  Per tile alpha:
@@ -172,6 +252,7 @@ inline size_t tile_smem_bytes(hc_dtype dt, int C) {
     case HC_FP64: return tile_smem_bytes_m<ModeF64>(C);
     case HC_FP32: return tile_smem_bytes_m<ModeF32>(C);
     case HC_FP32_MIXED: return tile_smem_bytes_m<ModeMixed>(C);
+    case HC_FP32_FF: return tile_smem_bytes_m<ModeFF>(C);
   }
   return 0;
 }
@@ -308,7 +389,7 @@ struct TileStages {
 
   // last stage, pencil r: interpolate group 0 and write the outputs to
   // out_tile (global), or back into the W tile (SMEM_OUT)
-  template <bool FINAL, bool SMEM_OUT>
+  template <bool FINAL, bool SMEM_OUT, int POL = kPolNone>
   static __device__ __forceinline__ void interp0(void* __restrict__ out_tile, unsigned char* smem,
                                                  int r) {
     constexpr int R = p3(C - S::g0);
@@ -323,11 +404,11 @@ struct TileStages {
     } else if constexpr (FINAL) {
       Out* o = reinterpret_cast<Out*>(out_tile);
 #pragma unroll
-      for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = M::out(v[j]);
+      for (int j = 0; j < p3(S::g0); ++j) st_pol<POL>(o + j * R + r, M::out(v[j]));
     } else {
       W* o = reinterpret_cast<W*>(out_tile);
 #pragma unroll
-      for (int j = 0; j < p3(S::g0); ++j) o[j * R + r] = v[j];
+      for (int j = 0; j < p3(S::g0); ++j) st_pol<POL>(o + j * R + r, v[j]);
     }
   }
 };
@@ -336,7 +417,8 @@ struct TileStages {
 // finished tile back into the W tile in shared memory (in place, each thread
 // its own pencils; out_tile unused) and fences it for the async proxy, so
 // that the caller can store it with one bulk copy.
-template <class M, int C, bool FINAL, class Loader, bool SMEM_OUT = false>
+// POL: L2 priority of the tile's global stores.
+template <class M, int C, bool FINAL, class Loader, bool SMEM_OUT = false, int POL = kPolNone>
 __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ out_tile,
                                           unsigned char* smem) {
   typedef typename M::In In;
@@ -363,11 +445,11 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
       if constexpr (FINAL) {
         Out* o = reinterpret_cast<Out*>(out_tile);
 #pragma unroll
-        for (int j = 0; j < p3(C); ++j) o[j] = M::out(w[j]);
+        for (int j = 0; j < p3(C); ++j) st_pol<POL>(o + j, M::out(w[j]));
       } else {
         W* o = reinterpret_cast<W*>(out_tile);
 #pragma unroll
-        for (int j = 0; j < p3(C); ++j) o[j] = w[j];
+        for (int j = 0; j < p3(C); ++j) st_pol<POL>(o + j, w[j]);
       }
     }
   } else {
@@ -386,7 +468,8 @@ __device__ __forceinline__ void tile_body(const Loader& ld, void* __restrict__ o
       __syncthreads();
     }
 #pragma unroll 1
-    for (int r = tid; r < St::kInterp0; r += nt) St::template interp0<FINAL, SMEM_OUT>(out_tile, smem, r);
+    for (int r = tid; r < St::kInterp0; r += nt)
+      St::template interp0<FINAL, SMEM_OUT, POL>(out_tile, smem, r);
     if constexpr (SMEM_OUT) {
       static_assert(!FINAL, "bulk tile stores write the intermediate W");
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -625,8 +708,9 @@ struct NoPtrs {};
 // interpolates the inner K2 axes in place in shared memory, round 2 the outer
 // K1 axes from shared memory to dst.  smem: 2 * 3^k * L W elements.
 // `tile(i, base, l0)` yields the position of tile i; n tiles in all.
+// LPOL / SPOL: L2 priorities of the element copies in and of the stores out.
 template <class M, int K1, int K2, int L, bool FINAL, class TileFn, bool TR = false,
-          class PtrFn = NoPtrs>
+          class PtrFn = NoPtrs, int LPOL = kPolNone, int SPOL = kPolNone>
 __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src0, void* dst0,
                                                        long long lo, int n, const TileFn& tile,
                                                        unsigned char* smem,
@@ -655,7 +739,7 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src0
 #pragma unroll 1
     for (int e = tid; e < NE; e += nt) {
       const int row = e / L, l = e - row * L;
-      if (l0 + l < lo) cp_async<sizeof(W)>(b + e, src + base + (long long)row * lo + l);
+      if (l0 + l < lo) cp_async_pol<sizeof(W), LPOL>(b + e, src + base + (long long)row * lo + l);
     }
     cp_async_commit();
   };
@@ -729,11 +813,12 @@ __device__ __forceinline__ void interp_tiles_pipelined(const typename M::W* src0
         Out* d = reinterpret_cast<Out*>(dst_);
 #pragma unroll
         for (int j = 0; j < p3(K1); ++j)
-          d[base + (long long)(j * p3(K2) + r) * lo + l] = M::out(v[j]);
+          st_pol<SPOL>(d + base + (long long)(j * p3(K2) + r) * lo + l, M::out(v[j]));
       } else {
         W* d = reinterpret_cast<W*>(dst_);
 #pragma unroll
-        for (int j = 0; j < p3(K1); ++j) d[base + (long long)(j * p3(K2) + r) * lo + l] = v[j];
+        for (int j = 0; j < p3(K1); ++j)
+          st_pol<SPOL>(d + base + (long long)(j * p3(K2) + r) * lo + l, v[j]);
       }
     }
     __syncthreads();  // b is refilled two tiles later

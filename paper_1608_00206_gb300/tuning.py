@@ -24,7 +24,8 @@ from ._lib import check
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_schedules.json")
 _DT = {"int64": (torch.int64, _lib.HC_INT64), "float64": (torch.float64, _lib.HC_FP64),
-       "float32": (torch.float32, _lib.HC_FP32), "mixed": (torch.float32, _lib.HC_FP32_MIXED)}
+       "float32": (torch.float32, _lib.HC_FP32), "mixed": (torch.float32, _lib.HC_FP32_MIXED),
+       "ff": (torch.float32, _lib.HC_FP32_FF)}
 _installed = set()
 _lock = threading.Lock()
 
@@ -103,7 +104,7 @@ def ensure_installed(device) -> None:
 def main():
     ap = argparse.ArgumentParser(description="tune schedules on this GPU")
     ap.add_argument("--dims", default="10-20")
-    ap.add_argument("--dtypes", default="int64,float64,float32,mixed")
+    ap.add_argument("--dtypes", default="int64,float64,float32,mixed,ff")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=TABLE)
     a = ap.parse_args()

@@ -73,6 +73,10 @@ def test_default_schedule_table(L):
 def test_status_strings(L):
     for s in range(8):
         assert L.hc_status_string(s).decode().startswith("HC_")
+    # the float-float dtype: x, y, z are float32; plain form only
+    assert L.hc_workspace_size(12, _lib.HC_FP32_FF) > 0
+    assert L.hc_backward_workspace_size(12, _lib.HC_FP32_FF) == 0
+    assert L.hc_workspace_size(5, 5) == 0
     assert L.hc_version() > 0
 
 
@@ -122,7 +126,7 @@ def test_argument_errors_caught_on_host(L):
     # workspace overlapping the output
     assert conv(x, y, zz, 20, _lib.HC_INT64, zz, big, None) == _lib.HC_ERR_ALIAS
     # explicit schedules out of range
-    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (3, 0, 0, 0), (1, 0, 0, 12), (-1, 0, 0, 0),
+    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (4, 0, 0, 0), (3, 0, 7, 0), (1, 0, 0, 12), (-1, 0, 0, 0),
                 (1, 0, 0, -8), (2, 0, 0, -64), (1, 8, 6, 16, 12), (1, 8, 6, 16, -8)]:
         s = _lib.hc_schedule(*bad)
         assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, ctypes.byref(s), ws, size,
@@ -140,7 +144,8 @@ def test_argument_errors_caught_on_host(L):
 
 # Largest D that hc_convolve_noalloc accepts per dtype, as include/hc.h states
 # it (16 MiB array, built-in chunked schedule).
-NOALLOC_LIMITS = {_lib.HC_INT64: 16, _lib.HC_FP64: 16, _lib.HC_FP32: 17, _lib.HC_FP32_MIXED: 13}
+NOALLOC_LIMITS = {_lib.HC_INT64: 16, _lib.HC_FP64: 16, _lib.HC_FP32: 17, _lib.HC_FP32_MIXED: 13,
+                  _lib.HC_FP32_FF: 13}
 
 
 @pytest.mark.parametrize("code,limit", sorted(NOALLOC_LIMITS.items()))

@@ -1,6 +1,8 @@
 """Accuracy of the precision forms, per D, against the float64 oracle (the
 mixed-precision row: binary32 evaluation and products with float-float
-interpolation, compared with plain binary32 and float64).
+interpolation; the float-float row: every value in float-float, the
+products from the FMA two-product; compared with plain binary32 and
+float64).
 
 For each D and input family the GPU results in float32, mixed and float64
 are compared with the oracle's float64 recurrence; the relative L-infinity
@@ -52,15 +54,26 @@ def test_error_per_D_against_float64_oracle(hc, family):
         scale = np.abs(ref).max()
         errs = {}
         for name, kw, xs, ys in (("fp32", {}, x32, y32), ("mixed", {"mixed": True}, x32, y32),
+                                 ("ff", {"mixed": "ff"}, x32, y32),
                                  ("fp64", {}, x32.astype(np.float64), y32.astype(np.float64))):
             z = _run(hc, xs, ys, **kw)
             err = np.abs(z - ref)
-            u = U64 if name == "fp64" else U32
-            bound = (oracle.gamma(3 * D + 1, u) + oracle.gamma(3 * D + 1, U64)) * za
+            if name == "ff":
+                # float-float operations (u about 2^-47, bounded with 2^-44),
+                # one binary32 rounding at the end, the float64 reference's own
+                bound = ((oracle.gamma(3 * D + 1, 2.0 ** -44) + oracle.gamma(3 * D + 1, U64)) * za
+                         + U32 * np.abs(ref))
+            else:
+                u = U64 if name == "fp64" else U32
+                bound = (oracle.gamma(3 * D + 1, u) + oracle.gamma(3 * D + 1, U64)) * za
             assert np.all(err <= bound), (family, D, name)
             errs[name] = float(err.max() / scale)
         assert errs["fp64"] == 0.0  # bitwise equal to the oracle's own recurrence
-        rows.append((D, errs["fp32"], errs["mixed"]))
-    print(f"\n{family}: D, rel. L-inf error vs float64 oracle (fp32, mixed)")
-    for D, e32, emx in rows:
-        print(f"  D={D:2d}  fp32 {e32:.3e}  mixed {emx:.3e}  ratio {e32 / max(emx, 1e-300):.2f}")
+        # float-float is within a few binary32 roundings of the scale, far
+        # below the forms that round products to binary32
+        assert errs["ff"] <= 4 * U32 and errs["ff"] <= errs["fp32"] / 10, (family, D)
+        rows.append((D, errs["fp32"], errs["mixed"], errs["ff"]))
+    print(f"\n{family}: D, rel. L-inf error vs float64 oracle (fp32, mixed, ff)")
+    for D, e32, emx, eff in rows:
+        print(f"  D={D:2d}  fp32 {e32:.3e}  mixed {emx:.3e}  ff {eff:.3e}  "
+              f"fp32/ff {e32 / max(eff, 1e-300):.0f}")

@@ -95,6 +95,34 @@ def test_mixed_bit_exact(hc, D):
     assert_bit_equal(gpu_conv(hc, x, y, mixed=True), oracle.convolve_mixed(x, y))
 
 
+@pytest.mark.parametrize("D", list(range(0, 14)))
+def test_ff_bit_exact(hc, D):
+    """Every value in float-float (HC_FP32_FF): bitwise the oracle's
+    float-float recurrence (same two-sum, FMA two-product and quick-two-sum
+    steps in the same order)."""
+    x, y = inputs.uniform01_pair(D, seed=500 + D)
+    assert_bit_equal(gpu_conv(hc, x, y, mixed="ff"), oracle.convolve_ff(x, y))
+
+
+@pytest.mark.parametrize("sched", [dict(c=3, kmax=2), dict(c=8, kmax=6), dict(c=7, kmax=4, cols=-32),
+                                   dict(c=8, m=3), dict(c=5, m=6), dict(c=8, m=6, bulk=True),
+                                   dict(c=7, m=4, bulk=True)])
+def test_ff_every_schedule(hc, sched):
+    """The float-float form through whole-array passes, the chunked engine and
+    the slab kernel (D = 15: outer passes after the chunks)."""
+    D = 15
+    x, y = inputs.normal_pair(D, seed=600 + int(sched["c"]), dtype=np.float32)
+    assert_bit_equal(gpu_conv(hc, x, y, mixed="ff", **sched), oracle.convolve_ff(x, y))
+
+
+def test_ff_integer_inputs_rounded_exact(hc):
+    """Integer inputs (values in [-2000, 2000], D = 12): the float-float form
+    returns the exact result rounded once to binary32 at every output."""
+    xi, yi = inputs.uniform_int_pair(12, -2000, 2000, seed=12)
+    got = gpu_conv(hc, xi.astype(np.float32), yi.astype(np.float32), mixed="ff")
+    assert_bit_equal(got, oracle.convolve(xi, yi).astype(np.float32))
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 @pytest.mark.parametrize("c,kmax", [(1, 1), (4, 2), (7, 5), (8, 6), (9, 6)])
 def test_fp_every_schedule(hc, dt, c, kmax):
@@ -131,6 +159,75 @@ def test_mixed_chunked_schedules(hc, c, m):
     D = 13
     x, y = inputs.uniform01_pair(D, seed=c + m)
     assert_bit_equal(gpu_conv(hc, x, y, mixed=True, c=c, m=m), oracle.convolve_mixed(x, y))
+
+
+@pytest.mark.parametrize("c", [7, 8, 5])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6])
+def test_int64_chunked_bulk_every_middle_depth(hc, c, m):
+    """Chunked-bulk schedule (every middle axis evaluated by the passes; the
+    slab kernel for c = 7, 8, the generic engine on the same plan for c = 5):
+    D = 15 gives 3^(15-c-m) units of 3^m tiles, up to 3 outer passes, ragged
+    column tickets (3^c columns in tickets of cpt * 8)."""
+    D = 15
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=300 + 10 * c + m)
+    assert_bit_equal(gpu_conv(hc, x, y, c=c, m=m, bulk=True), oracle.convolve(x, y, threads=16))
+
+
+@pytest.mark.parametrize("kind,c,m", [("float64", 8, 6), ("float64", 7, 3), ("float32", 9, 6),
+                                      ("float32", 8, 4), ("float32", 9, 1), ("mixed", 8, 6),
+                                      ("mixed", 7, 5), ("mixed", 8, 2)])
+def test_fp_chunked_bulk_schedules(hc, kind, c, m):
+    """The slab kernel in every floating-point mode: same per-element order
+    as the recurrence, so bitwise the oracle (mixed: float-float
+    intermediates in the workspace, the columns or the last pass round)."""
+    D = 15
+    if kind == "mixed":
+        x, y = inputs.uniform01_pair(D, seed=c + 10 * m)
+        want = oracle.convolve_mixed(x, y)
+    else:
+        x, y = inputs.normal_pair(D, seed=c + 10 * m,
+                                  dtype=np.float64 if kind == "float64" else np.float32)
+        want = oracle.convolve(x, y, threads=16)
+    assert_bit_equal(gpu_conv(hc, x, y, mixed=(kind == "mixed"), c=c, m=m, bulk=True), want)
+
+
+@pytest.mark.parametrize("D,m", [(14, 6), (12, 4), (9, 1)])
+def test_chunked_bulk_single_unit(hc, D, m):
+    """D = c + m: one unit, the columns write the final result (no outer
+    pass); int64 and float32."""
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=D)
+    assert_bit_equal(gpu_conv(hc, x, y, c=D - m, m=m, bulk=True), oracle.convolve(x, y, threads=8))
+    xf, yf = inputs.normal_pair(D, seed=D, dtype=np.float32)
+    assert_bit_equal(gpu_conv(hc, xf, yf, c=D - m, m=m, bulk=True),
+                     oracle.convolve(xf, yf, threads=8))
+
+
+def test_chunked_bulk_managed_output_falls_back(hc):
+    """A managed output takes the generic engine on the chunked-bulk plan
+    (no bulk copies into managed memory): same bits."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib
+    rt = _cudart()
+    D = 14
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=77)
+    lib = _lib.lib()
+    s = _lib.hc_schedule(_lib.HC_SCHED_CHUNKED_BULK, 8, 4, 0, 0)
+    nb = int(lib.hc_workspace_size_schedule(D, _lib.HC_INT64, ctypes.byref(s)))
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=DEV)
+    xd, yd = T(x), T(y)
+    ptr = ctypes.c_void_p()
+    assert rt.cudaMallocManaged(ctypes.byref(ptr), ctypes.c_size_t(8 * 3 ** D), 1) == 0
+    try:
+        st = torch.cuda.current_stream().cuda_stream
+        assert lib.hc_convolve_schedule(xd.data_ptr(), yd.data_ptr(), ptr.value, D, _lib.HC_INT64,
+                                        ctypes.byref(s), ws.data_ptr(), nb, st) == 0
+        torch.cuda.synchronize()
+        got = np.ctypeslib.as_array((ctypes.c_byte * (8 * 3 ** D)).from_address(ptr.value))
+        assert_bit_equal(got.view(np.int64).copy(), oracle.convolve(x, y, threads=8))
+    finally:
+        torch.cuda.synchronize()
+        rt.cudaFree(ptr)
 
 
 @pytest.mark.parametrize("cols", [8, 16, 32, -16, -32])
@@ -222,18 +319,20 @@ def test_d16_fp64_separable_closed_form(hc):
     assert np.all(np.abs(z - z_closed) <= bound)
 
 
-@pytest.mark.parametrize("D", [17, 18, 19, 20])
-def test_int64_full_size(hc, D):
+@pytest.mark.parametrize("D,bulk", [(17, False), (18, False), (19, False), (20, False),
+                                    (18, True), (20, True)])
+def test_int64_full_size(hc, D, bulk):
     """D = 17..20 int64, values in [-1000, 1000] (the benchmark workload and
     its sweep, with the tuned schedule of each D, the launch configuration
     the benchmark times): 3^D outputs, 27.9 GB at D = 20.  Checked on whole
     slices (four prefix digits fixed, the oracle's (D-4)-D recurrence on the
     matching sub-cube pairs, summed over the pairs of the digit-1 axes), on
     random single outputs (the definition), and on the sum invariant over all
-    outputs."""
+    outputs.  bulk: the chunked-bulk schedule (8-axis tiles, 6 middle axes
+    per L2-resident unit, one outer pass) instead of the tuned default."""
     x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2000 + D)
     xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
-    z = hc.convolve(xt, yt)
+    z = hc.convolve(xt, yt, **({'c': 8, 'm': 6, 'bulk': True, 'cols': 32} if bulk else {}))
     torch.cuda.synchronize()
     # sum invariant (no overflow: |sum z| <= (2^20 * 1000)^2)
     assert int(z.sum().item()) == int(x.sum()) * int(y.sum())

@@ -475,3 +475,55 @@ def test_pins_catch_planted_mistakes(oracle, mutation):
     if mutation in ("order", "interleave"):
         assert np.array(_py_rec(list(e4), list(e6), mutation)).argmax() != 21
     assert np.array(_py_rec(list(e4), list(e6))).argmax() == 21
+
+
+# ------------------------------------------------------- float-float form
+
+
+def test_ff_hand_example(oracle):
+    """x = y = (4097, 1): z = (4097^2, 2 * 4097, 1) = (16785409, 8194, 1).  In
+    binary32 the product 4097^2 = 2^24 + 8193 rounds (ties to even) to
+    16785408, so plain binary32 and the float-float-interpolation form both
+    end at z[1] = (4098^2 - 16785408) - 1 = 8195.  The float-float form keeps
+    the product's low part (4097^2 - 16785408 = 1, from the FMA two-product)
+    and gets z[1] = 8194 exactly; z[0] rounds once, to 16785408."""
+    x = np.array([4097, 1], np.float32)
+    zf = oracle.convolve_ff(x, x)
+    assert zf.tolist() == [16785408.0, 8194.0, 1.0]
+    assert oracle.convolve(x, x)[1] == 8195.0
+    assert oracle.convolve_mixed(x, x)[1] == 8195.0
+
+
+@pytest.mark.parametrize("D,r", [(4, 4000), (8, 4000), (10, 2000), (12, 1000)])
+def test_ff_is_the_rounded_exact_result_on_integer_inputs(oracle, D, r):
+    """Integer inputs: every sum, product and difference of the recurrence is
+    an integer that a float-float pair holds exactly here, so the form returns
+    the exact result (the int64 oracle) rounded once to binary32, at every
+    output -- while binary32 products lose bits (plain binary32 and the
+    mixed form miss outputs)."""
+    xi, yi = inputs.uniform_int_pair(D, -r, r, seed=D)
+    want = oracle.convolve(xi, yi).astype(np.float32)
+    x, y = xi.astype(np.float32), yi.astype(np.float32)
+    assert np.array_equal(oracle.convolve_ff(x, y), want)
+    assert np.count_nonzero(oracle.convolve(x, y) != want) > 0
+    assert np.count_nonzero(oracle.convolve_mixed(x, y) != want) > 0
+
+
+@pytest.mark.parametrize("D", [6, 10, 12])
+def test_ff_within_float_float_bound(oracle, D):
+    """Dyadic U[0,1) inputs (exact result from the int64 oracle): the error is
+    one final binary32 rounding plus the float-float rounding of the 3D + 1
+    operations on the longest path, bounded with u = 2^-44 (the float-float
+    operations' unit roundoff is about 2^-47)."""
+    g = np.random.default_rng(D)
+    xi = inputs.dyadic(g.random(1 << D), 10)
+    yi = inputs.dyadic(g.random(1 << D), 10)
+    z_exact = oracle.convolve(xi, yi).astype(np.float64) / float(1 << 20)
+    x, y = (xi / 1024.0).astype(np.float32), (yi / 1024.0).astype(np.float32)
+    zf = oracle.convolve_ff(x, y).astype(np.float64)
+    za = oracle.zabs(x, y)
+    assert np.all(np.abs(zf - z_exact) <= oracle.gamma(3 * D + 1, 2.0 ** -44) * za
+                  + U32 * np.abs(z_exact))
+    # and far inside the binary32 bound the other forms need
+    z32 = oracle.convolve(x, y).astype(np.float64)
+    assert np.max(np.abs(zf - z_exact)) < np.max(np.abs(z32 - z_exact))
