@@ -323,6 +323,7 @@ ChunkPlan make_chunk_plan(int D, hc_dtype dt, int c_req, int m_req, bool bulk) {
     const long long coltiles = ((long long)pow3z(C) + p.L - 1) / p.L;
     long long cpt = 32768 / ((long long)pow3z(p.m) * p.L);
     if (cpt < 1) cpt = 1;
+    if (bulk && (cpt & 1)) ++cpt;  // the slab kernel's column tiles are 2 * L wide
     p.cpt = (int)cpt;
     p.n_cols = (int)((coltiles + cpt - 1) / cpt);
   } else {

@@ -54,12 +54,18 @@ struct SlabArgs {
 };
 
 // Shared memory: two W tiles (TileBulk's layout), which the column tickets
-// reuse for their two column tiles, then the two row buffers, placed above
+// reuse for their column tile, then the two row buffers, placed above
 // whichever of the two is larger.
+// Columns per column tile of the slab kernel: 16 (128-byte row segments for
+// 8-byte intermediates), twice the generic engine's 8, whose 64-byte segments
+// halve what each load instruction moves.  A ticket's cpt * 8 columns are an
+// even number, i.e. whole tiles except at the end of a unit's 3^C columns.
+constexpr int kSlabCols = 16;
+
 template <class M, int C, int MM>
 struct SlabSmem {
   static constexpr size_t kCols =
-      MM <= 3 ? 0 : 2 * sizeof(typename M::W) * (size_t)p3(MM) * kPersistCols;
+      MM <= 3 ? 0 : sizeof(typename M::W) * (size_t)p3(MM) * kSlabCols;
   static constexpr size_t kRowsOff =
       TileBulk<M, C>::kOff > kCols ? TileBulk<M, C>::kOff : (kCols + 15) / 16 * 16;
   static constexpr size_t bytes = kRowsOff + 2 * 2 * sizeof(typename M::In) * (size_t)p2(C);
@@ -225,13 +231,12 @@ __global__ void __launch_bounds__(256, (sizeof(typename M::W) == 4 ? 3 : 2))
         if constexpr (MM <= 3) {
           cols_small_k<M, MM, FIN, kPolStream, LP>(src, dst, c0, c1, N);
         } else {
-          const int n = (int)((c1 - c0 + L - 1) / L);
-          auto tile = [&](int i, long long& base, long long& l0) {
-            l0 = c0 + (long long)i * L;
-            base = l0;
-          };
-          interp_tiles_pipelined<M, MM - 3, 3, L, FIN, decltype(tile), false, NoPtrs, LP,
-                                 kPolStream>(src, dst, N, n, tile, smem);
+          // one 3^m x 16 tile at a time: round 1 loads its pencils straight
+          // from L2 into registers (27 independent loads per thread)
+#pragma unroll 1
+          for (long long l0 = c0; l0 < c1; l0 += kSlabCols)
+            interp_tile_body<M, MM - 3, 3, kSlabCols, FIN, true, false, LP, kPolStream>(
+                src, dst, l0, l0, N, smem);
         }
       }
       __syncthreads();  // s_tk, s_ok and shared memory reused by the next ticket

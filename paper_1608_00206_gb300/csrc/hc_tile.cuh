@@ -598,7 +598,10 @@ __device__ __forceinline__ void tile_loop_bulk(SrcFn src, OutFn out, long long n
 // written by other CTAs of the same launch).
 // TR: the transposed map I^T (outer K1 axes first, then the inner K2 axes,
 // each pencil transformed outermost axis first) -- the adjoint's pass.
-template <class M, int K1, int K2, int L, bool FINAL, bool CG, bool TR = false>
+// LPOL / SPOL (non-transposed, K1 > 0): L2 priorities of the global loads
+// (CG only) and of the stores.
+template <class M, int K1, int K2, int L, bool FINAL, bool CG, bool TR = false,
+          int LPOL = kPolNone, int SPOL = kPolNone>
 __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void* dst_,
                                                  long long base, long long l0, long long lo,
                                                  unsigned char* smem) {
@@ -665,7 +668,13 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
         if (l0 + l >= lo) continue;
         W v[p3(K2)];
 #pragma unroll
-        for (int j = 0; j < p3(K2); ++j) v[j] = ldw<CG>(src + base + (long long)(o * p3(K2) + j) * lo + l);
+        for (int j = 0; j < p3(K2); ++j) {
+          const W* a = src + base + (long long)(o * p3(K2) + j) * lo + l;
+          if constexpr (CG)
+            v[j] = ld_cg_pol<LPOL>(a);
+          else
+            v[j] = *a;
+        }
         interp_pencil<M, K2>(v);
 #pragma unroll
         for (int j = 0; j < p3(K2); ++j) T[(o * p3(K2) + j) * L + l] = v[j];
@@ -684,11 +693,12 @@ __device__ __forceinline__ void interp_tile_body(const typename M::W* src, void*
           Out* d = reinterpret_cast<Out*>(dst_);
 #pragma unroll
           for (int j = 0; j < p3(K1); ++j)
-            d[base + (long long)(j * p3(K2) + r) * lo + l] = M::out(v[j]);
+            st_pol<SPOL>(d + base + (long long)(j * p3(K2) + r) * lo + l, M::out(v[j]));
         } else {
           W* d = reinterpret_cast<W*>(dst_);
 #pragma unroll
-          for (int j = 0; j < p3(K1); ++j) d[base + (long long)(j * p3(K2) + r) * lo + l] = v[j];
+          for (int j = 0; j < p3(K1); ++j)
+            st_pol<SPOL>(d + base + (long long)(j * p3(K2) + r) * lo + l, v[j]);
         }
       }
       __syncthreads();  // shared tile reused by the caller's next tile
