@@ -11,6 +11,7 @@ Workloads (--workload):
              [-1000, 1000]; z has 3^20 = 3.49e9 int64 outputs (27.9 GB)
   d16_fp64   D = 16 float64 probability hypercubes (Exponential(1) / sum)
   d16_mixed  the same inputs in float32, float-float interpolation
+  d16_ff     the same inputs in float32, every value in float-float
   d10_int64  D = 10 int64, values in [-100, 100]
   batched    4096 float32 instances, D ~ U{6..14}, U[0,1) inputs; fused
              persistent launch + per-D grouped passes at the autotuned fusion
@@ -47,6 +48,8 @@ WORKLOADS = {
                 "to sum 1; z 3^16 float64",
     "d16_mixed": "D=16 float32 probability hypercubes, float32 evaluation and products, "
                  "float-float interpolation",
+    "d16_ff": "D=16 float32 probability hypercubes, every value in float-float (two-sum "
+              "evaluation, FMA two-product, two-sum interpolation)",
     "d10_int64": "D=10 int64 exact: x,y 1024 iid uniform integers in [-100,100]",
     "d18_fp32": "D=18 float32: x,y 2^18 iid U[0,1); z 3^18 float32",
     "batched": "4096 float32 instances, D iid uniform in 6..14, x,y iid U[0,1); fused "
@@ -55,9 +58,9 @@ WORKLOADS = {
     "fwdbwd": "D=18 float32, x,y,w iid N(0,1), loss = sum(w*z), forward + hand-written adjoint "
               "via torch.autograd",
 }
-DEFAULT_STEPS = {"d20_int64": 30, "d16_fp64": 30, "d16_mixed": 50, "d10_int64": 200,
+DEFAULT_STEPS = {"d20_int64": 30, "d16_fp64": 30, "d16_mixed": 50, "d16_ff": 50, "d10_int64": 200,
                  "d18_fp32": 50, "batched": 20, "fwdbwd": 30}
-SINGLE = ("d20_int64", "d16_fp64", "d16_mixed", "d10_int64", "d18_fp32")
+SINGLE = ("d20_int64", "d16_fp64", "d16_mixed", "d16_ff", "d10_int64", "d18_fp32")
 
 
 def _peaks():
@@ -71,8 +74,31 @@ def _peaks():
 
 # FP64 throughput of GB300 from the nominal dense FP64 rate (1.25 TFLOP/s,
 # counting a fused multiply-add as two): 0.625e12 FP64 add, subtract or
-# multiply instructions per second.
-FP64_OPS_PEAK = 0.625e12
+# multiply instructions per second -- context only; the roofline's FP64 peak
+# is measured on the device by hc_probe_alu_rate (see _fp64_peak).
+FP64_OPS_NOMINAL = 0.625e12
+_FP64_MEASURED = []
+
+
+def _fp64_peak():
+    """(ops/s, source): FP64 add/multiply rate measured on this device by the
+    library's probe kernel (independent add/multiply chains, CUDA events),
+    once per process; the nominal rate if the probe fails."""
+    if not _FP64_MEASURED:
+        import ctypes
+
+        import torch
+
+        from paper_1608_00206_gb300 import _lib
+        v = ctypes.c_double()
+        rc = _lib.lib().hc_probe_alu_rate(_lib.HC_FP64, ctypes.byref(v),
+                                          torch.cuda.current_stream().cuda_stream)
+        _FP64_MEASURED.append(float(v.value) if rc == 0 and v.value > 0 else None)
+    m = _FP64_MEASURED[0]
+    if m is None:
+        return FP64_OPS_NOMINAL, "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2)"
+    return m, ("measured FP64 add/multiply rate of this device (hc_probe_alu_rate: "
+               "independent __dadd_rn/__dmul_rn chains, CUDA events)")
 L2_BYTES = 129 << 20  # GB300 L2 (rounded up)
 L2_FLUSH_BYTES = 256 << 20
 
@@ -193,14 +219,14 @@ class Workload:
             x, y = inputs.uniform01_pair(D, seed)
             self._single(D, x, y, torch.float32, mixed=False)
             self.dtype = "f32"
-        elif name in ("d16_fp64", "d16_mixed"):
+        elif name in ("d16_fp64", "d16_mixed", "d16_ff"):
             D = D_override or 16
             x, y = inputs.prob_exponential_pair(D, seed)
-            if name == "d16_mixed":
+            if name != "d16_fp64":
                 x, y = x.astype(np.float32), y.astype(np.float32)
             self._single(D, x, y, torch.float64 if name == "d16_fp64" else torch.float32,
-                         mixed=(name == "d16_mixed"))
-            self.dtype = "f64" if name == "d16_fp64" else "f32+ff"
+                         mixed={"d16_mixed": True, "d16_ff": "ff"}.get(name, False))
+            self.dtype = _dtype_name(name)
         elif name == "batched":
             dims = inputs.batched_dims(4096, 6, 14, seed)
             pairs = inputs.batched_uniform01(dims, seed + 1)
@@ -282,7 +308,7 @@ class Workload:
 
         from paper_1608_00206_gb300 import _lib
         code = {"d20_int64": 0, "d10_int64": 0, "d16_fp64": 1, "d18_fp32": 2,
-                "d16_mixed": 3}[self.name]
+                "d16_mixed": 3, "d16_ff": 4}[self.name]
         cmax = 9 if code == 2 else 8
         if self.sched:
             kind = (3 if self.sched.get("bulk") else 2) if "m" in self.sched else 1
@@ -303,8 +329,8 @@ class Workload:
         D = self.D
         if self.name == "batched":
             return self._batched_bytes(kname) / max(launches_per_step, 1), "hbm"
-        s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64") else 4
-        sw = 8 if self.name == "d16_mixed" else s
+        s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64", "d16_ff") else 4
+        sw = 8 if self.name in ("d16_mixed", "d16_ff") else s
         if kname in ("chunk", "slab"):
             kind, C, m, ap, ev = self.schedule_geometry()
             if self.name == "d16_fp64":
@@ -327,7 +353,7 @@ class Workload:
         if kname in ("interp_pass", "interp_t_pass"):
             return 2 * 3 ** D * sw, "hbm"  # read and write the whole 3^D array
         if kname in ("tile_conv", "tile_adj"):
-            C = min(D, 9 if (s == 4 and self.name != "d16_mixed" and kname == "tile_conv") else 8)
+            C = min(D, 9 if (s == 4 and sw == 4 and kname == "tile_conv") else 8)
             a = D - C
             return 3 ** D * sw + 2 * 3 ** a * 2 ** C * s, "hbm"
         return None, "hbm"
@@ -491,12 +517,19 @@ def _comparisons(wl, ms_per_step):
         x, y = wl.x.detach(), wl.y.detach()
         t = timed(lambda: hc.convolve(x, y), reps=5)
         return {"forward_only_ms": t, "fwdbwd_over_forward": ms_per_step / t}
-    if wl.name == "d16_mixed":
+    if wl.name in ("d16_mixed", "d16_ff"):
         z = torch.empty(3 ** wl.D, dtype=torch.float32, device=wl.dev)
         nb = hc.workspace_size(wl.D, torch.float32)
         ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=wl.dev)
         t = timed(lambda: hc.convolve(wl.x, wl.y, out=z, workspace=ws), reps=10)
-        return {"plain_fp32_ms": t, "mixed_over_plain_fp32": ms_per_step / t}
+        key = "mixed" if wl.name == "d16_mixed" else "ff"
+        out = {"plain_fp32_ms": t, f"{key}_over_plain_fp32": ms_per_step / t}
+        if wl.name == "d16_ff":
+            nbm = hc.workspace_size(wl.D, torch.float32, True)
+            wsm = torch.empty(max(nbm, 256), dtype=torch.uint8, device=wl.dev)
+            tm = timed(lambda: hc.convolve(wl.x, wl.y, out=z, mixed=True, workspace=wsm), reps=10)
+            out.update({"mixed_ms": tm, "ff_over_mixed": ms_per_step / tm})
+        return out
     return None
 
 
@@ -617,11 +650,12 @@ def _oracle_samples(name):
                 samples.append((lambda xs=xs, ys=ys: oracle.convolve(xs, ys, threads=thr).size))
         return ("slices z[d1,d2,:] (d1,d2 in {0,2}) of the D=20 problem: the 18-D recurrence on "
                 "the matching sub-cubes, 3^18 outputs each", samples, thr)
-    if name in ("d16_fp64", "d16_mixed"):
+    if name in ("d16_fp64", "d16_mixed", "d16_ff"):
         x, y = inputs.prob_exponential_pair(16, seed)
-        if name == "d16_mixed":
+        if name != "d16_fp64":
             x32, y32 = x.astype(np.float32), y.astype(np.float32)
-            f = lambda: oracle.convolve_mixed(x32, y32).size  # noqa: E731
+            fn = oracle.convolve_mixed if name == "d16_mixed" else oracle.convolve_ff
+            f = lambda: fn(x32, y32).size  # noqa: E731
             return "the full D=16 problem (single thread)", [f], 1
         return "the full D=16 problem", [lambda: oracle.convolve(x, y, threads=thr).size], thr
     if name == "d18_fp32":
@@ -692,7 +726,7 @@ def _reference_arm(args, rank, world):
 
 def _dtype_name(w):
     return {"d20_int64": "int64", "d10_int64": "int64", "d16_fp64": "f64", "d16_mixed": "f32+ff",
-            "d18_fp32": "f32", "batched": "f32", "fwdbwd": "f32"}[w]
+            "d16_ff": "ff", "d18_fp32": "f32", "batched": "f32", "fwdbwd": "f32"}[w]
 
 
 # ------------------------------------------------------------------- main
@@ -714,11 +748,12 @@ def _roofline(wl, prof, steps):
                 "unit": "GB/s", "frac": None, "traffic": None}
     if bound == "alu":
         achieved = alg / (per_launch_ms / 1e3) / 1e12
+        peak, source = _fp64_peak()
         return {"bound": "alu", "kernel": kname, "achieved": achieved,
-                "peak": FP64_OPS_PEAK / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / (FP64_OPS_PEAK / 1e12), "traffic": None,
-                "ms_per_launch": per_launch_ms,
-                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2)"}
+                "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (peak / 1e12), "traffic": None,
+                "ms_per_launch": per_launch_ms, "peak_source": source,
+                "frac_of_nominal": achieved / (FP64_OPS_NOMINAL / 1e12)}
     achieved = alg / (per_launch_ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak_hbm,
             "unit": "GB/s", "frac": achieved / peak_hbm,
@@ -751,7 +786,7 @@ SWEEP_STEPS = {14: 200, 15: 100, 16: 60, 17: 40, 18: 30, 19: 20}
 # The training-system forms beside the plain method, each timed after the
 # headline: (workload, steps).
 FORMS = (("batched", 20), ("fwdbwd", 30), ("d16_fp64", 30), ("d16_mixed", 50),
-         ("d18_fp32", 50))
+         ("d16_ff", 50), ("d18_fp32", 50))
 
 
 def _brief(res):

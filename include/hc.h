@@ -385,6 +385,18 @@ int hc_profile_collect(char* names, int name_len, double* total_ms, int* counts,
                        int max_kernels);
 
 /* ------------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper): the device's rate of the
+ * dtype's round-to-nearest add and multiply instructions, the operations of
+ * the recurrence, for the roofline of the arithmetic-bound float64 path.  A
+ * kernel of 8 independent add/multiply chains per thread, 8 CTAs of 256
+ * threads per SM, is timed with CUDA events on `stream` (best of three after
+ * a warm-up; synchronises); *ops_per_s receives the operations per second.
+ * It allocates and frees its own small output array, so it is not for
+ * allocation-free regions.  HC_FP64 and HC_FP32 only (HC_ERR_DTYPE
+ * otherwise); HC_ERR_ARG for a NULL result pointer. */
+hc_status hc_probe_alu_rate(hc_dtype dtype, double* ops_per_s, hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Status word kept in the first bytes of every workspace.  Synchronises
  * `stream`, then returns HC_OK or the error a kernel recorded there
  * (HC_ERR_TIMEOUT).  HC_ERR_ARG for a NULL workspace.

@@ -16,6 +16,8 @@ and marshals numpy arrays.  Functions and the passages they follow:
   ``direct_last_axis=True`` uses the 3-product D = 1 base case instead).
 * :func:`convolve_mixed` -- the same recurrence with binary32 evaluation and
   products and float-float interpolation.
+* :func:`convolve_direct_top` -- the hybrid form: 4-way direct form on the
+  top ``mt`` axes, Karatsuba recurrence (Kronecker form) on the others.
 * :func:`convolve_ff` -- the same recurrence with every value in float-float
   (two-sum evaluation, FMA two-product, two-sum interpolation), binary32 in
   and out.
@@ -69,6 +71,7 @@ def _lib():
             lib.oracle_recurrence.argtypes = [vp, vp, vp, i, i, i, i]
             lib.oracle_recurrence_mixed.argtypes = [vp, vp, vp, i]
             lib.oracle_recurrence_ff.argtypes = [vp, vp, vp, i]
+            lib.oracle_direct_top.argtypes = [vp, vp, vp, i, i, i]
             lib.oracle_recurrence_inplace.argtypes = [vp, vp, vp, i, i, i]
             lib.oracle_adjoint.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_adjoint_brute.argtypes = [vp, vp, vp, vp, vp, i, i]
@@ -181,6 +184,17 @@ def convolve_mixed(x, y) -> np.ndarray:
     D = dim_of(x)
     z = np.empty(3 ** D, dtype=np.float32)
     _lib().oracle_recurrence_mixed(_ptr(x), _ptr(y), _ptr(z), D)
+    return z
+
+
+def convolve_direct_top(x, y, mt: int) -> np.ndarray:
+    """The hybrid form: on the top mt axes the 4-way direct form (products of
+    sub-cube pairs summed, no interpolation), on the other D - mt axes the
+    Karatsuba form; mt = 0 is the recurrence, mt = D Algorithm 1."""
+    x, y, D, code = _prep(x, y)
+    z = np.empty(3 ** D, dtype=x.dtype)
+    if _lib().oracle_direct_top(_ptr(x), _ptr(y), _ptr(z), D, int(mt), code):
+        raise RuntimeError("oracle_direct_top failed")
     return z
 
 

@@ -275,6 +275,84 @@ void rec_mixed(const float* x, const float* y, ff* z, int D, float* scratch) {
 }
 
 // ---------------------------------------------------------------------------
+// Hybrid form: the 4-way direct form on the top mt axes (Methods: z[1] =
+// x[0]*y[1] + x[1]*y[0] needs no interpolation), the Karatsuba recurrence on
+// the other n = D - mt axes, written as the Kronecker form the recurrence
+// unrolls to.  For each top digit string a (axis 1 first):
+//   P_a = sum over the pairs (b, c) of top bit strings with b + c = a of
+//         (E^{(x)n} x_b) (.) (E^{(x)n} y_c),
+//   z_a = I^{(x)n} P_a,
+// where x_b is the sub-cube of x whose top bits are b.  Digit 0 takes bits
+// (0, 0), digit 2 takes (1, 1), digit 1 takes (0, 1) or (1, 0); the pairs are
+// summed in the order of increasing x index (the first pair of each digit-1
+// axis gives x bit 0).  E is applied axis by axis outermost first and I
+// innermost first, the recurrence's own per-element order, so mt = 0 is the
+// recurrence bit for bit and mt = D is Algorithm 1's summation bit for bit.
+
+// E^{(x)n} of one 2^n sub-cube into 3^n values, outermost axis first.
+template <class T>
+void kron_eval(const T* x, T* out, int n, T* scratch) {
+  if (n == 0) {
+    out[0] = x[0];
+    return;
+  }
+  const size_t h = (size_t)1 << (n - 1), m = pow3(n - 1);
+  T* s = scratch;
+  for (size_t k = 0; k < h; ++k) s[k] = x[k] + x[h + k];
+  kron_eval(x, out, n - 1, scratch + h);
+  kron_eval(s, out + m, n - 1, scratch + h);
+  kron_eval(x + h, out + 2 * m, n - 1, scratch + h);
+}
+
+// I^{(x)n} in place on 3^n values, innermost axis first.
+template <class T>
+void kron_interp(T* p, int n) {
+  if (n == 0) return;
+  const size_t m = pow3(n - 1);
+  kron_interp(p, n - 1);
+  kron_interp(p + m, n - 1);
+  kron_interp(p + 2 * m, n - 1);
+  for (size_t k = 0; k < m; ++k) p[m + k] = (p[m + k] - p[k]) - p[2 * m + k];
+}
+
+template <class T>
+void direct_top(const T* x, const T* y, T* z, int D, int mt) {
+  const int n = D - mt;
+  const size_t n2 = (size_t)1 << n, n3 = pow3(n);
+  std::vector<T> xe(n3), ye(n3), acc(n3), scratch(2 * n2 + 2);
+  for (size_t a = 0; a < pow3(mt); ++a) {
+    int dig[64];
+    size_t aa = a;
+    for (int d = mt - 1; d >= 0; --d) {
+      dig[d] = (int)(aa % 3);
+      aa /= 3;
+    }
+    int ones[64], m1 = 0;
+    size_t base = 0;  // top bits fixed by digits 2
+    for (int d = 0; d < mt; ++d) {
+      const size_t bit = (size_t)1 << (mt - 1 - d);
+      if (dig[d] == 2) base |= bit;
+      if (dig[d] == 1) ones[m1++] = d;
+    }
+    for (size_t sidx = 0; sidx < ((size_t)1 << m1); ++sidx) {
+      size_t bx = base, by = base;
+      for (int q = 0; q < m1; ++q) {
+        const size_t bit = (size_t)1 << (mt - 1 - ones[q]);
+        if ((sidx >> (m1 - 1 - q)) & 1u) bx |= bit; else by |= bit;
+      }
+      kron_eval(x + bx * n2, xe.data(), n, scratch.data());
+      kron_eval(y + by * n2, ye.data(), n, scratch.data());
+      for (size_t j = 0; j < n3; ++j) {
+        const T p = xe[j] * ye[j];
+        acc[j] = sidx == 0 ? p : acc[j] + p;
+      }
+    }
+    kron_interp(acc.data(), n);
+    for (size_t j = 0; j < n3; ++j) z[a * n3 + j] = acc[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Float-float form: every value of the recurrence -- the inputs' sums
 // (evaluation), the products and the interpolation -- is a float-float pair
 // (h, l) of binary32 values, rounded to binary32 once at the end.  The
@@ -483,6 +561,16 @@ int oracle_recurrence_mixed(const float* x, const float* y, float* z, int D) {
   rec_mixed(x, y, w.data(), D, scratch.data());
   for (size_t k = 0; k < w.size(); ++k) z[k] = w[k].h + w[k].l;
   return 0;
+}
+
+int oracle_direct_top(const void* x, const void* y, void* z, int D, int mt, int dtype) {
+  if (mt < 0 || mt > D) return 1;
+  switch (dtype) {
+    case 0: direct_top((const u64*)x, (const u64*)y, (u64*)z, D, mt); return 0;
+    case 1: direct_top((const double*)x, (const double*)y, (double*)z, D, mt); return 0;
+    case 2: direct_top((const float*)x, (const float*)y, (float*)z, D, mt); return 0;
+  }
+  return 1;
 }
 
 int oracle_recurrence_ff(const float* x, const float* y, float* z, int D) {

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hc_batched_autotune": (_i, [ctypes.POINTER(hc_instance), _i, _i, _vp, _sz, _i, _vp,
                                  ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)]),
     "hc_device_status": (_i, [_vp, _vp]),
+    "hc_probe_alu_rate": (_i, [_i, ctypes.POINTER(ctypes.c_double), _vp]),
     "hc_profile_enable": (_i, [_i]),
     "hc_profile_collect": (_i, [_cp, _i, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int), _i]),

@@ -527,3 +527,45 @@ def test_ff_within_float_float_bound(oracle, D):
     # and far inside the binary32 bound the other forms need
     z32 = oracle.convolve(x, y).astype(np.float64)
     assert np.max(np.abs(zf - z_exact)) < np.max(np.abs(z32 - z_exact))
+
+
+# ---------------------------------------------------------------- hybrid form
+
+
+@pytest.mark.parametrize("D", [1, 4, 7, 9])
+def test_direct_top_int64_equals_brute_force_for_every_split(oracle, D):
+    """The hybrid form (4-way direct form on the top mt axes, Karatsuba on
+    the rest) is exact in Z/2^64 for every mt: Algorithm 1's result."""
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=900 + D)
+    want = oracle.brute_force(x, y)
+    for mt in range(D + 1):
+        assert np.array_equal(oracle.convolve_direct_top(x, y, mt), want), mt
+
+
+@pytest.mark.parametrize("D", [3, 6, 8])
+def test_direct_top_float_end_points(oracle, D):
+    """Floating point: with no direct axes it is the recurrence bit for bit,
+    with every axis direct it is Algorithm 1's summation bit for bit (pairs
+    summed in increasing x index, as the brute force visits them)."""
+    for dt in (np.float64, np.float32):
+        x, y = inputs.normal_pair(D, seed=910 + D, dtype=dt)
+        assert np.array_equal(oracle.convolve_direct_top(x, y, 0).view(np.uint8),
+                              oracle.convolve(x, y).view(np.uint8))
+        assert np.array_equal(oracle.convolve_direct_top(x, y, D).view(np.uint8),
+                              oracle.brute_force(x, y).view(np.uint8))
+
+
+@pytest.mark.parametrize("D,mt", [(8, 3), (10, 4), (10, 2)])
+def test_direct_top_within_forward_bound(oracle, D, mt):
+    """Dyadic inputs (exact result from the int64 oracle): float32 hybrid
+    results stay within gamma_{3D+1}(2^-24) * zabs (the direct axes replace
+    the Karatsuba ones' sums and differences by at most as many additions of
+    terms no larger in magnitude)."""
+    g = np.random.default_rng(D + mt)
+    xi = inputs.dyadic(g.random(1 << D), 10)
+    yi = inputs.dyadic(g.random(1 << D), 10)
+    z_exact = oracle.convolve(xi, yi).astype(np.float64) / float(1 << 20)
+    x, y = (xi / 1024.0).astype(np.float32), (yi / 1024.0).astype(np.float32)
+    zh = oracle.convolve_direct_top(x, y, mt).astype(np.float64)
+    za = oracle.zabs(x, y)
+    assert np.all(np.abs(zh - z_exact) <= oracle.gamma(3 * D + 1, U32) * za)
