@@ -310,6 +310,9 @@ class Workload:
         code = {"d20_int64": 0, "d10_int64": 0, "d16_fp64": 1, "d18_fp32": 2,
                 "d16_mixed": 3, "d16_ff": 4}[self.name]
         cmax = 9 if code == 2 else 8
+        if self.sched.get("top"):
+            C = min(self.sched.get("c") or 8, self.D - self.sched["top"])
+            return 4, C, self.sched["top"], self.D - self.sched["top"] - C, 0
         if self.sched:
             kind = (3 if self.sched.get("bulk") else 2) if "m" in self.sched else 1
             c, k = self.sched.get("c", 0), self.sched.get("m", self.sched.get("kmax", 0))
@@ -352,6 +355,11 @@ class Workload:
             return self._fp64_ops(kname, launches_per_step), "alu"
         if kname in ("interp_pass", "interp_t_pass"):
             return 2 * 3 ** D * sw, "hbm"  # read and write the whole 3^D array
+        if kname == "hybrid_tile":
+            # write the 3^D outputs; read a pair of rows per sub-cube pair:
+            # 4^top pairs of top strings x 3^a middle rows of 2^C elements
+            _, C, top, a, _ = self.schedule_geometry()
+            return 3 ** D * sw + 2 * 4 ** top * 3 ** a * 2 ** C * s, "hbm"
         if kname in ("tile_conv", "tile_adj"):
             C = min(D, 9 if (s == 4 and sw == 4 and kname == "tile_conv") else 8)
             a = D - C
@@ -855,7 +863,8 @@ def main():
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
-                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked|bulk) "
+                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked|bulk; "
+                         "hybrid:c:k:cols:cols_outer:top) "
                          "instead of the tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
     if args.D is not None and args.workload not in SINGLE + ("fwdbwd",):
@@ -891,12 +900,16 @@ def main():
         if args.workload not in SINGLE:
             ap.error("--schedule applies to single-instance workloads only")
         kind, c, k, cols, *outer = args.schedule.split(":")
-        if kind not in ("passes", "chunked", "bulk"):
-            ap.error("schedule kind is passes, chunked or bulk")
+        if kind not in ("passes", "chunked", "bulk", "hybrid"):
+            ap.error("schedule kind is passes, chunked, bulk or hybrid")
         wl.sched = {"c": int(c), "cols": int(cols),
-                    ("kmax" if kind == "passes" else "m"): int(k)}
+                    ("kmax" if kind in ("passes", "hybrid") else "m"): int(k)}
         if kind == "bulk":
             wl.sched["bulk"] = True
+        if kind == "hybrid":
+            if len(outer) != 2:
+                ap.error("hybrid schedules are hybrid:c:k:cols:cols_outer:top")
+            wl.sched["top"] = int(outer[1])
         if outer:
             wl.sched["cols_outer"] = int(outer[0])
         nb = wl.hc.workspace_size(wl.D, wl.z.dtype, wl.mixed, **wl.sched)

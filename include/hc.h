@@ -143,6 +143,21 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  *                      intermediate in managed or host-mapped memory, or c
  *                      other than 7 or 8, runs the CHUNKED kernel on the
  *                      same plan (same bits).
+ *   HC_SCHED_HYBRID  : the 4-way direct form on the top `top` axes (1..6):
+ *                      for each digit string of those axes the tile sums the
+ *                      products of the x and y sub-cube pairs that add up to
+ *                      it (Methods: z[1] = x[0]*y[1] + x[1]*y[0], no
+ *                      interpolation on that axis), then the Karatsuba form
+ *                      on the D - top axes below (c tile axes, at most 8; the
+ *                      middle axes in whole-array passes of at most k).
+ *                      (4/3)^top times the evaluation and product work of
+ *                      the other schedules, `top` fewer axes to interpolate
+ *                      over HBM.  HC_INT64, HC_FP64 and HC_FP32 only.  Its
+ *                      floating-point results are bitwise those of this
+ *                      hybrid form (pairs summed in increasing x index),
+ *                      which differ from the plain recurrence's rounding;
+ *                      int64 results are Algorithm 1's.  HC_ERR_ARG when
+ *                      D - top < 4.
  *   HC_SCHED_DEFAULT : the per-(D, dtype) default (built in: CHUNKED with
  *                      default sizes; replaced by hc_set_default_schedule,
  *                      typically with hc_autotune's winner).
@@ -159,6 +174,7 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
 #define HC_SCHED_PASSES 1
 #define HC_SCHED_CHUNKED 2
 #define HC_SCHED_CHUNKED_BULK 3
+#define HC_SCHED_HYBRID 4
 
 typedef struct {
   int kind;
@@ -166,6 +182,7 @@ typedef struct {
   int k;
   int cols;
   int cols_outer;  /* width of the pass over the outermost axes; 0 = cols */
+  int top;         /* HC_SCHED_HYBRID: direct-form top axes; 0 for the others */
 } hc_schedule;
 
 size_t hc_workspace_size_schedule(int D, hc_dtype dtype, const hc_schedule* s);

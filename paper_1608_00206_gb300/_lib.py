@@ -20,14 +20,16 @@ _vp, _i, _sz, _cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_cha
 
 
 HC_SCHED_DEFAULT, HC_SCHED_PASSES, HC_SCHED_CHUNKED, HC_SCHED_CHUNKED_BULK = 0, 1, 2, 3
+HC_SCHED_HYBRID = 4
 
 
 class hc_schedule(ctypes.Structure):
-    _fields_ = [("kind", _i), ("c", _i), ("k", _i), ("cols", _i), ("cols_outer", _i)]
+    _fields_ = [("kind", _i), ("c", _i), ("k", _i), ("cols", _i), ("cols_outer", _i),
+                ("top", _i)]
 
     def as_dict(self):
         return {"kind": self.kind, "c": self.c, "k": self.k, "cols": self.cols,
-                "cols_outer": self.cols_outer}
+                "cols_outer": self.cols_outer, "top": self.top}
 
 
 class hc_instance(ctypes.Structure):

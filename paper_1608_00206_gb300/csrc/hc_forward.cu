@@ -383,13 +383,19 @@ cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, voi
 namespace hc {
 
 static std::mutex g_sched_mu;
-static hc_schedule g_default[HC_MAX_D + 1][4];
-static bool g_has_default[HC_MAX_D + 1][4];
+constexpr int kNumDtypes = 5;  // HC_INT64 .. HC_FP32_FF
+static hc_schedule g_default[HC_MAX_D + 1][kNumDtypes];
+static bool g_has_default[HC_MAX_D + 1][kNumDtypes];
 
 bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
   const int cmax = dtype == HC_FP32 ? 9 : 8;
-  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_CHUNKED_BULK) return false;
+  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_HYBRID) return false;
   if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
+  if (s.kind == HC_SCHED_HYBRID) {
+    if (s.top < 1 || s.top > 6 || s.c > 8 || !hybrid_dtype_ok(dtype)) return false;
+  } else if (s.top != 0) {
+    return false;
+  }
   auto width_ok = [](int w) {
     return w == 0 || w == 8 || w == 16 || w == 32 || w == -16 || w == -32;
   };
@@ -398,8 +404,8 @@ bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
 
 hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
   if (s && s->kind != HC_SCHED_DEFAULT) return *s;
-  hc_schedule r = {HC_SCHED_CHUNKED, 0, 0, 0, 0};
-  if (D >= 0 && D <= HC_MAX_D && dtype >= 0 && dtype < 4) {
+  hc_schedule r = {HC_SCHED_CHUNKED, 0, 0, 0, 0, 0};
+  if (D >= 0 && D <= HC_MAX_D && dtype >= 0 && dtype < kNumDtypes) {
     std::lock_guard<std::mutex> g(g_sched_mu);
     if (g_has_default[D][dtype]) r = g_default[D][dtype];
   }
@@ -430,8 +436,19 @@ static size_t widen_bytes(int D, hc_dtype dtype) {
   return dtype == HC_FP32_FF ? 2 * align_up(sizeof(ffv) << D, 256) : 0;
 }
 
+static HybPlan hybrid_plan(int D, hc_dtype dt, const hc_schedule& s) {
+  HybPlan p = make_hybrid_plan(D, dt, s.top, s.c, s.k);
+  p.cols = s.cols;
+  p.cols_outer = s.cols_outer;
+  return p;
+}
+
 static size_t plan_ws(int D, hc_dtype dtype, const hc_schedule& s) {
   if (s.kind == HC_SCHED_PASSES || D == 0) return passes_plan(D, dtype, s).ws_bytes;
+  if (s.kind == HC_SCHED_HYBRID) {
+    const HybPlan h = hybrid_plan(D, dtype, s);
+    return h.ok ? h.ws_bytes : 0;
+  }
   return chunked_plan(D, dtype, s).ws_bytes;
 }
 
@@ -450,6 +467,8 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
   if (!x || !y || !z) return HC_ERR_ARG;
   if (!aligned(x, 16) || !aligned(y, 16) || !aligned(z, 16)) return HC_ERR_ALIGN;
   const hc_schedule s = resolve_schedule(D, dtype, sched);
+  if (s.kind == HC_SCHED_HYBRID && D > 0 && !hybrid_plan(D, dtype, s).ok)
+    return HC_ERR_ARG;  // fewer than 4 tile axes below the direct ones
   const size_t need = schedule_ws(D, dtype, s);
   if (ws_bytes < need) return HC_ERR_WORKSPACE;
   if (need > 0 && !workspace) return HC_ERR_ARG;
@@ -488,6 +507,9 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
   if (s.kind == HC_SCHED_PASSES || D == 0)
     return record_cuda_error(forward_dispatch(passes_plan(D, dtype, s), x, y, z,
                                               (unsigned char*)workspace, stream, w));
+  if (s.kind == HC_SCHED_HYBRID)
+    return record_cuda_error(hybrid_dispatch(hybrid_plan(D, dtype, s), x, y, z,
+                                             (unsigned char*)workspace, stream, w));
   return record_cuda_error(chunk_dispatch(chunked_plan(D, dtype, s), x, y, z,
                                           (unsigned char*)workspace, stream, w));
 }
@@ -508,6 +530,16 @@ static std::vector<hc_schedule> tune_candidates(int D, hc_dtype dtype) {
         v.push_back({HC_SCHED_CHUNKED, c, k, cols[ci], 0});
         v.push_back({HC_SCHED_CHUNKED_BULK, c, k, cols[ci], 0});
       }
+  }
+  // the hybrid form: 2..4 direct top axes, 8-axis tiles, the middle axes in
+  // passes of 5 or 6
+  if (hybrid_dtype_ok(dtype)) {
+    for (int top = 2; top <= 4; ++top)
+      for (int k = 5; k <= 6; ++k)
+        for (int w : {32, -32}) {
+          const hc_schedule h = {HC_SCHED_HYBRID, 8, k, w, 0, top};
+          if (D - top >= 4) v.push_back(h);
+        }
   }
   return v;
 }

@@ -62,6 +62,25 @@ cudaError_t chunk_forward_mix(const ChunkPlan& p, const void* x, const void* y, 
 cudaError_t chunk_forward_ff(const ChunkPlan& p, const void* x, const void* y, void* z,
                              unsigned char* ws, cudaStream_t st, void* w = nullptr);
 
+// The hybrid schedule (hc_hybrid.cu): direct form on the top mt axes.
+struct HybPlan {
+  int D, mt, C, a;
+  hc_dtype dtype;
+  int n_eval;
+  int eval_d0[HC_MAX_D], eval_k[HC_MAX_D];
+  bool eval_to_final[HC_MAX_D];
+  int n_interp;
+  int interp_d0[HC_MAX_D], interp_k[HC_MAX_D];
+  size_t off_xo, off_yo, off_tx, off_ty;
+  size_t ws_bytes;
+  int cols, cols_outer;
+  bool ok;  // false: mt outside 1..6 or fewer than 4 tile axes left
+};
+HybPlan make_hybrid_plan(int D, hc_dtype dt, int mt, int c_req, int kmax_req);
+bool hybrid_dtype_ok(hc_dtype dt);
+cudaError_t hybrid_dispatch(const HybPlan& p, const void* x, const void* y, void* z,
+                            unsigned char* ws, cudaStream_t st, void* w);
+
 // c_req, kmax_req <= 0 select the defaults (largest tile, 6 axes per pass).
 FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);
 

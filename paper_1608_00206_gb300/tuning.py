@@ -78,7 +78,8 @@ def install(table) -> int:
     for dt, entries in table.get("schedules", {}).items():
         code = _DT[dt][1]
         for D, s in entries.items():
-            sched = _lib.hc_schedule(s["kind"], s["c"], s["k"], s["cols"], s.get("cols_outer", 0))
+            sched = _lib.hc_schedule(s["kind"], s["c"], s["k"], s["cols"], s.get("cols_outer", 0),
+                                     s.get("top", 0))
             check(lib.hc_set_default_schedule(int(D), code, ctypes.byref(sched)),
                   "hc_set_default_schedule")
             n += 1

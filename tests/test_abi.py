@@ -60,7 +60,7 @@ def test_default_schedule_table(L):
     assert L.hc_set_default_schedule(20, _lib.HC_INT64, ctypes.byref(s)) == 0
     try:
         assert L.hc_get_default_schedule(20, _lib.HC_INT64, ctypes.byref(got)) == 0
-        assert got.as_dict() == {"kind": 1, "c": 8, "k": 6, "cols": 16, "cols_outer": 0}
+        assert got.as_dict() == {"kind": 1, "c": 8, "k": 6, "cols": 16, "cols_outer": 0, "top": 0}
         assert L.hc_workspace_size(20, _lib.HC_INT64) == \
             L.hc_workspace_size_schedule(20, _lib.HC_INT64, ctypes.byref(s))
         assert L.hc_workspace_size(19, _lib.HC_INT64) != 0  # other entries untouched
@@ -126,7 +126,8 @@ def test_argument_errors_caught_on_host(L):
     # workspace overlapping the output
     assert conv(x, y, zz, 20, _lib.HC_INT64, zz, big, None) == _lib.HC_ERR_ALIAS
     # explicit schedules out of range
-    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (4, 0, 0, 0), (3, 0, 7, 0), (1, 0, 0, 12), (-1, 0, 0, 0),
+    for bad in [(1, 9, 0, 0), (2, 0, 7, 0), (5, 0, 0, 0), (3, 0, 7, 0), (1, 0, 0, 12), (-1, 0, 0, 0),
+                (4, 8, 6, 0, 0, 0), (4, 9, 6, 0, 0, 3), (4, 8, 6, 0, 0, 7), (1, 8, 6, 0, 0, 2),
                 (1, 0, 0, -8), (2, 0, 0, -64), (1, 8, 6, 16, 12), (1, 8, 6, 16, -8)]:
         s = _lib.hc_schedule(*bad)
         assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, ctypes.byref(s), ws, size,
@@ -140,6 +141,15 @@ def test_argument_errors_caught_on_host(L):
     assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, None, ws, size, None) == \
         _lib.HC_ERR_ARG
     assert L.hc_device_status(None, None) == _lib.HC_ERR_ARG
+    # the hybrid schedule: fewer than 4 axes below the direct ones, or a
+    # float-float dtype
+    s = _lib.hc_schedule(_lib.HC_SCHED_HYBRID, 8, 6, 0, 0, 7)
+    assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_INT64, ctypes.byref(s), ws, size,
+                                  None) == _lib.HC_ERR_ARG
+    s = _lib.hc_schedule(_lib.HC_SCHED_HYBRID, 8, 6, 0, 0, 2)
+    assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_FP32_MIXED, ctypes.byref(s), ws, size,
+                                  None) == _lib.HC_ERR_ARG
+    assert L.hc_workspace_size_schedule(10, _lib.HC_INT64, ctypes.byref(s)) > 0
 
 
 # Largest D that hc_convolve_noalloc accepts per dtype, as include/hc.h states

@@ -230,6 +230,69 @@ def test_chunked_bulk_managed_output_falls_back(hc):
         rt.cudaFree(ptr)
 
 
+@pytest.mark.parametrize("dt", [np.int64, np.float64, np.float32])
+@pytest.mark.parametrize("D,top,c,kmax", [(9, 1, 8, 6), (10, 2, 8, 6), (12, 3, 5, 4),
+                                          (13, 4, 8, 2), (14, 6, 4, 3), (15, 3, 8, 6),
+                                          (16, 2, 7, 5)])
+def test_hybrid_bit_exact(hc, dt, D, top, c, kmax):
+    """Hybrid schedule (direct form on the top axes): bitwise the oracle's
+    hybrid form in every dtype, and Algorithm 1 in int64.  Covers a final
+    tile with no middle axes (D = top + c), ragged pairs (up to 2^6 per
+    tile) and one to three middle passes."""
+    if dt is np.int64:
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=700 + D + top)
+    else:
+        x, y = inputs.normal_pair(D, seed=700 + D + top, dtype=dt)
+    want = oracle.convolve_direct_top(x, y, top)
+    got = gpu_conv(hc, x, y, top=top, c=c, kmax=kmax, cols=-32 if D % 2 else 32)
+    assert_bit_equal(got, want)
+    if dt is np.int64:
+        assert_bit_equal(got, oracle.convolve(x, y, threads=8))
+
+
+def test_hybrid_d18_float32_workload(hc):
+    """The D = 18 float32 workload with 3 direct axes (one 6-axis middle
+    pass).  A slice whose top digits hold no 1 has a single sub-cube pair, so
+    it is the plain recurrence on that pair: bitwise the oracle's.  Slices
+    with digit-1 axes sum 2, 4 or 8 pairs' products: within the float32
+    forward bound of the exact slice (the pairs' float64 recurrences)."""
+    D, top = 18, 3
+    x, y = inputs.uniform01_pair(D, seed=1818)
+    z = hc.convolve(T(x), T(y), top=top, c=8, kmax=6, cols=32).cpu().numpy()
+    n, h = 3 ** (D - top), 1 << (D - top)
+    for a in (0, 26, 8, 18, 13, 5):
+        digits = [a // 9 % 3, a // 3 % 3, a % 3]
+        ones = [i for i, d in enumerate(digits) if d == 1]
+        parts, pairs = [], []
+        for sidx in range(1 << len(ones)):
+            bx = [d // 2 for d in digits]
+            by = [d // 2 for d in digits]
+            for q, i in enumerate(ones):
+                if (sidx >> (len(ones) - 1 - q)) & 1:
+                    bx[i] = 1
+                else:
+                    by[i] = 1
+            ox = sum(b << (top - 1 - i) for i, b in enumerate(bx)) * h
+            oy = sum(b << (top - 1 - i) for i, b in enumerate(by)) * h
+            parts.append(oracle.convolve(x[ox:ox + h], y[oy:oy + h], threads=16) if not ones
+                         else None)
+            pairs.append((ox, oy))
+        got = z[a * n:(a + 1) * n]
+        if not ones:
+            assert_bit_equal(got, parts[0])
+        else:
+            # float64 pair recurrences summed (error far below float32's);
+            # the bound: gamma_{3D+1}(2^-24) times the pairs' magnitudes
+            want = np.zeros(n)
+            za = np.zeros(n)
+            for (ox, oy) in pairs:
+                xs, ys = x[ox:ox + h].astype(np.float64), y[oy:oy + h].astype(np.float64)
+                want += oracle.convolve(xs, ys, threads=16)
+                za += oracle.zabs(xs, ys)
+            err = np.abs(got.astype(np.float64) - want)
+            assert np.all(err <= oracle.gamma(3 * D + 1, 2.0 ** -24) * za), a
+
+
 @pytest.mark.parametrize("cols", [8, 16, 32, -16, -32])
 @pytest.mark.parametrize("kind", ["int64", "float64", "float32", "mixed"])
 def test_every_interpolation_tile_width(hc, kind, cols):
