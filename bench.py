@@ -525,6 +525,15 @@ def _comparisons(wl, ms_per_step):
         x, y = wl.x.detach(), wl.y.detach()
         t = timed(lambda: hc.convolve(x, y), reps=5)
         return {"forward_only_ms": t, "fwdbwd_over_forward": ms_per_step / t}
+    if wl.name == "d18_fp32" and wl.D == 18:
+        # the hybrid schedule: 4 direct-form top axes leave one
+        # 6-axis middle pass; its own rounding, so never a default
+        nb = hc.workspace_size(wl.D, torch.float32, top=4, c=8, kmax=6, cols=32)
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=wl.dev)
+        z = torch.empty(3 ** wl.D, dtype=torch.float32, device=wl.dev)
+        t = timed(lambda: hc.convolve(wl.x, wl.y, out=z, workspace=ws, top=4, c=8, kmax=6,
+                                      cols=32), reps=10)
+        return {"hybrid_top4_ms": t, "hybrid_over_default": t / ms_per_step}
     if wl.name in ("d16_mixed", "d16_ff"):
         z = torch.empty(3 ** wl.D, dtype=torch.float32, device=wl.dev)
         nb = hc.workspace_size(wl.D, torch.float32)

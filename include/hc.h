@@ -157,7 +157,9 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  *                      hybrid form (pairs summed in increasing x index),
  *                      which differ from the plain recurrence's rounding;
  *                      int64 results are Algorithm 1's.  HC_ERR_ARG when
- *                      D - top < 4.
+ *                      D - top < 4.  Because its rounding differs, the
+ *                      autotuner considers it for HC_INT64 only, and a
+ *                      floating-point default schedule is never hybrid.
  *   HC_SCHED_DEFAULT : the per-(D, dtype) default (built in: CHUNKED with
  *                      default sizes; replaced by hc_set_default_schedule,
  *                      typically with hc_autotune's winner).
@@ -193,7 +195,9 @@ hc_status hc_convolve_schedule(const void* x, const void* y, void* z, int D, hc_
 
 /* The schedule hc_convolve and hc_workspace_size use for (D, dtype);
  * s = NULL restores the built-in choice.  Process-wide, thread-safe; a
- * workspace sized before a change may no longer be large enough. */
+ * workspace sized before a change may no longer be large enough.
+ * HC_ERR_ARG for a hybrid schedule with a floating-point dtype (a default
+ * never changes the recurrence's rounding). */
 hc_status hc_set_default_schedule(int D, hc_dtype dtype, const hc_schedule* s);
 
 hc_status hc_get_default_schedule(int D, hc_dtype dtype, hc_schedule* s);

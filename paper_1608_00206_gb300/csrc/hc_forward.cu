@@ -531,9 +531,11 @@ static std::vector<hc_schedule> tune_candidates(int D, hc_dtype dtype) {
         v.push_back({HC_SCHED_CHUNKED_BULK, c, k, cols[ci], 0});
       }
   }
-  // the hybrid form: 2..4 direct top axes, 8-axis tiles, the middle axes in
-  // passes of 5 or 6
-  if (hybrid_dtype_ok(dtype)) {
+  // the hybrid form (2..4 direct top axes, 8-axis tiles, the middle axes in
+  // passes of 5 or 6) only where it gives the same bits as the recurrence:
+  // int64.  A default schedule never changes a floating-point result's
+  // rounding; the hybrid form stays available by explicit request.
+  if (dtype == HC_INT64) {
     for (int top = 2; top <= 4; ++top)
       for (int k = 5; k <= 6; ++k)
         for (int w : {32, -32}) {
@@ -602,6 +604,8 @@ extern "C" hc_status hc_convolve_out(const void* x, const void* y, void* w, void
 extern "C" hc_status hc_set_default_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
   if (D < 0 || D > HC_MAX_D || hc::elem_size(dtype) == 0) return HC_ERR_ARG;
   if (s && (!hc::schedule_valid(*s, dtype) || s->kind == HC_SCHED_DEFAULT)) return HC_ERR_ARG;
+  // a default keeps the recurrence's bits: no hybrid form for floating point
+  if (s && s->kind == HC_SCHED_HYBRID && dtype != HC_INT64) return HC_ERR_ARG;
   std::lock_guard<std::mutex> g(hc::g_sched_mu);
   hc::g_has_default[D][dtype] = s != nullptr;
   if (s) hc::g_default[D][dtype] = *s;

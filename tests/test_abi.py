@@ -150,6 +150,10 @@ def test_argument_errors_caught_on_host(L):
     assert L.hc_convolve_schedule(x, y, z, 10, _lib.HC_FP32_MIXED, ctypes.byref(s), ws, size,
                                   None) == _lib.HC_ERR_ARG
     assert L.hc_workspace_size_schedule(10, _lib.HC_INT64, ctypes.byref(s)) > 0
+    # a default schedule keeps the recurrence's rounding: hybrid for int64 only
+    assert L.hc_set_default_schedule(10, _lib.HC_FP32, ctypes.byref(s)) == _lib.HC_ERR_ARG
+    assert L.hc_set_default_schedule(10, _lib.HC_INT64, ctypes.byref(s)) == _lib.HC_OK
+    assert L.hc_set_default_schedule(10, _lib.HC_INT64, None) == _lib.HC_OK
 
 
 # Largest D that hc_convolve_noalloc accepts per dtype, as include/hc.h states
