@@ -310,6 +310,10 @@ class Workload:
         code = {"d20_int64": 0, "d10_int64": 0, "d16_fp64": 1, "d18_fp32": 2,
                 "d16_mixed": 3, "d16_ff": 4}[self.name]
         cmax = 9 if code == 2 else 8
+        if self.sched.get("lowmem"):
+            # leaves of D - top axes on the whole-array-pass plan
+            C = min(self.sched.get("c") or 8, self.D - self.sched["top"])
+            return 1, C, 0, self.D - C, self.D - C
         if self.sched.get("top"):
             C = min(self.sched.get("c") or 8, self.D - self.sched["top"])
             return 4, C, self.sched["top"], self.D - self.sched["top"] - C, 0
@@ -320,6 +324,11 @@ class Workload:
             s = _lib.hc_schedule()
             _lib.lib().hc_get_default_schedule(self.D, code, ctypes.byref(s))
             kind, c, k = s.kind, s.c, s.k
+            if kind in (4, 5):  # hybrid / low-workspace defaults (int64)
+                C = min(c or 8, self.D - s.top)
+                if kind == 5:
+                    return 1, C, 0, self.D - C, self.D - C
+                return 4, C, s.top, self.D - s.top - C, 0
         C = min(c or cmax, self.D)
         if kind == 1:
             return kind, C, 0, self.D - C, self.D - C
@@ -873,7 +882,7 @@ def main():
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
                     help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked|bulk; "
-                         "hybrid:c:k:cols:cols_outer:top) "
+                         "hybrid|lowmem:c:k:cols:cols_outer:top) "
                          "instead of the tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
     if args.D is not None and args.workload not in SINGLE + ("fwdbwd",):
@@ -909,16 +918,17 @@ def main():
         if args.workload not in SINGLE:
             ap.error("--schedule applies to single-instance workloads only")
         kind, c, k, cols, *outer = args.schedule.split(":")
-        if kind not in ("passes", "chunked", "bulk", "hybrid"):
-            ap.error("schedule kind is passes, chunked, bulk or hybrid")
+        if kind not in ("passes", "chunked", "bulk", "hybrid", "lowmem"):
+            ap.error("schedule kind is passes, chunked, bulk, hybrid or lowmem")
         wl.sched = {"c": int(c), "cols": int(cols),
-                    ("kmax" if kind in ("passes", "hybrid") else "m"): int(k)}
+                    ("kmax" if kind in ("passes", "hybrid", "lowmem") else "m"): int(k)}
         if kind == "bulk":
             wl.sched["bulk"] = True
-        if kind == "hybrid":
+        if kind in ("hybrid", "lowmem"):
             if len(outer) != 2:
-                ap.error("hybrid schedules are hybrid:c:k:cols:cols_outer:top")
+                ap.error(f"{kind} schedules are {kind}:c:k:cols:cols_outer:top")
             wl.sched["top"] = int(outer[1])
+            wl.sched["lowmem"] = kind == "lowmem"
         if outer:
             wl.sched["cols_outer"] = int(outer[0])
         nb = wl.hc.workspace_size(wl.D, wl.z.dtype, wl.mixed, **wl.sched)

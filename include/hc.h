@@ -160,6 +160,22 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  *                      D - top < 4.  Because its rounding differs, the
  *                      autotuner considers it for HC_INT64 only, and a
  *                      floating-point default schedule is never hybrid.
+ *   HC_SCHED_LOWMEM  : the low-workspace form of the paper's recursion: the
+ *                      top `top` axes (1..6) are split one leaf at a time --
+ *                      for each of their 3^top digit strings a small kernel
+ *                      sums the input sub-cubes that the digits select (the
+ *                      leaf's evaluated inputs, 2^(D - top) elements each)
+ *                      and the leaf, a convolution of D - top axes, runs
+ *                      the PASSES schedule (c, k, per-element row copies)
+ *                      into z's slice -- then passes of at most k axes
+ *                      (width cols_outer) interpolate the top axes.
+ *                      Workspace: the two leaf inputs (2^(D - top) each)
+ *                      and one leaf's own workspace (its operands evaluated
+ *                      on its D - top - c outer axes) -- a few MB at D = 20
+ *                      with top = 6, against the gigabytes of the other
+ *                      schedules.  Same bits as every other schedule;
+ *                      3^top leaves of about five launches each.  HC_INT64,
+ *                      HC_FP64 and HC_FP32 only; HC_ERR_ARG when D <= top.
  *   HC_SCHED_DEFAULT : the per-(D, dtype) default (built in: CHUNKED with
  *                      default sizes; replaced by hc_set_default_schedule,
  *                      typically with hc_autotune's winner).
@@ -177,6 +193,7 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
 #define HC_SCHED_CHUNKED 2
 #define HC_SCHED_CHUNKED_BULK 3
 #define HC_SCHED_HYBRID 4
+#define HC_SCHED_LOWMEM 5
 
 typedef struct {
   int kind;
@@ -184,7 +201,8 @@ typedef struct {
   int k;
   int cols;
   int cols_outer;  /* width of the pass over the outermost axes; 0 = cols */
-  int top;         /* HC_SCHED_HYBRID: direct-form top axes; 0 for the others */
+  int top;         /* HC_SCHED_HYBRID: direct-form top axes; HC_SCHED_LOWMEM:
+                      top axes split leaf by leaf; 0 for the other kinds */
 } hc_schedule;
 
 size_t hc_workspace_size_schedule(int D, hc_dtype dtype, const hc_schedule* s);

@@ -29,6 +29,10 @@
 #include "hc_persist.cuh"
 #include "hc_tile.cuh"
 
+#ifndef HC_GROUP4_WIDE
+#define HC_GROUP4_WIDE 1
+#endif
+
 namespace hc {
 
 // counters[0]: ticket counter; counters[1 + i]: finished tiles of instance i.
@@ -148,7 +152,9 @@ __global__ void __launch_bounds__(256) group_tile_bulk_kernel(const GroupPtrs* _
 // register prefetch, or one tile at a time), each tile on its instance's
 // arrays.
 template <class M, int K1, int K2, int L, bool FINAL>
-__global__ void __launch_bounds__(K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256)
+__global__ void __launch_bounds__(K1 > 0 ? ((p3(K2) * L + 31) / 32 * 32 < 1024
+                                                 ? (p3(K2) * L + 31) / 32 * 32 : 1024)
+                                          : 256)
     group_interp_kernel(const GroupPtrs* __restrict__ tab, long long lo, long long per,
                         long long ntiles) {
   typedef typename M::W W;
@@ -430,10 +436,17 @@ template <class M, int K1, int K2, bool FINAL>
 static cudaError_t launch_group_interp_k(const GroupPtrs* tab, int n, long long lo,
                                          cudaStream_t st) {
   // columns per tile: 32, except 16 for 8-byte intermediates below 6 axes
-  // (two 16-column buffers double-buffer at two CTAs per SM)
-  constexpr int L = K1 == 0 ? 256 : (sizeof(typename M::W) == 8 && K1 + K2 < 6 ? 16 : 32);
+  // (two 16-column buffers double-buffer at two CTAs per SM) and, with
+  // HC_GROUP4_WIDE, 64 for 4-byte ones over 4 axes (81-row tiles: 32
+  // columns leave each CTA only 10 KB in flight)
+  constexpr int L = K1 == 0 ? 256
+                    : (sizeof(typename M::W) == 8 && K1 + K2 < 6
+                           ? 16
+                           : (HC_GROUP4_WIDE && sizeof(typename M::W) == 4 && K1 + K2 == 4 ? 64
+                                                                                          : 32));
   constexpr size_t smem = K1 > 0 ? InterpPipe<M, K1, K2, L>::kSmem : 0;
-  constexpr int threads = K1 > 0 ? (p3(K2) * L + 31) / 32 * 32 : 256;
+  constexpr int tw = (p3(K2) * L + 31) / 32 * 32;
+  constexpr int threads = K1 > 0 ? (tw < 1024 ? tw : 1024) : 256;
   auto k = group_interp_kernel<M, K1, K2, L, FINAL>;
   ProfileScope prof(st, "batched_interp");
   cudaError_t e = prep_kernel(k, smem);

@@ -389,10 +389,12 @@ static bool g_has_default[HC_MAX_D + 1][kNumDtypes];
 
 bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
   const int cmax = dtype == HC_FP32 ? 9 : 8;
-  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_HYBRID) return false;
+  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_LOWMEM) return false;
   if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
   if (s.kind == HC_SCHED_HYBRID) {
     if (s.top < 1 || s.top > 6 || s.c > 8 || !hybrid_dtype_ok(dtype)) return false;
+  } else if (s.kind == HC_SCHED_LOWMEM) {
+    if (s.top < 1 || s.top > 6 || !hybrid_dtype_ok(dtype)) return false;
   } else if (s.top != 0) {
     return false;
   }
@@ -443,8 +445,16 @@ static HybPlan hybrid_plan(int D, hc_dtype dt, const hc_schedule& s) {
   return p;
 }
 
+static LowPlan lowmem_plan(int D, hc_dtype dt, const hc_schedule& s) {
+  return make_lowmem_plan(D, dt, s.top, s.c, s.k, s.cols, s.cols_outer);
+}
+
 static size_t plan_ws(int D, hc_dtype dtype, const hc_schedule& s) {
   if (s.kind == HC_SCHED_PASSES || D == 0) return passes_plan(D, dtype, s).ws_bytes;
+  if (s.kind == HC_SCHED_LOWMEM) {
+    const LowPlan l = lowmem_plan(D, dtype, s);
+    return l.ok ? l.ws_bytes : 0;
+  }
   if (s.kind == HC_SCHED_HYBRID) {
     const HybPlan h = hybrid_plan(D, dtype, s);
     return h.ok ? h.ws_bytes : 0;
@@ -469,6 +479,8 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
   const hc_schedule s = resolve_schedule(D, dtype, sched);
   if (s.kind == HC_SCHED_HYBRID && D > 0 && !hybrid_plan(D, dtype, s).ok)
     return HC_ERR_ARG;  // fewer than 4 tile axes below the direct ones
+  if (s.kind == HC_SCHED_LOWMEM && D > 0 && !lowmem_plan(D, dtype, s).ok)
+    return HC_ERR_ARG;  // no axis left below the top ones
   const size_t need = schedule_ws(D, dtype, s);
   if (ws_bytes < need) return HC_ERR_WORKSPACE;
   if (need > 0 && !workspace) return HC_ERR_ARG;
@@ -509,6 +521,9 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
                                               (unsigned char*)workspace, stream, w));
   if (s.kind == HC_SCHED_HYBRID)
     return record_cuda_error(hybrid_dispatch(hybrid_plan(D, dtype, s), x, y, z,
+                                             (unsigned char*)workspace, stream, w));
+  if (s.kind == HC_SCHED_LOWMEM)
+    return record_cuda_error(lowmem_dispatch(lowmem_plan(D, dtype, s), x, y, z,
                                              (unsigned char*)workspace, stream, w));
   return record_cuda_error(chunk_dispatch(chunked_plan(D, dtype, s), x, y, z,
                                           (unsigned char*)workspace, stream, w));

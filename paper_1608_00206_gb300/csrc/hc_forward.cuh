@@ -81,6 +81,23 @@ bool hybrid_dtype_ok(hc_dtype dt);
 cudaError_t hybrid_dispatch(const HybPlan& p, const void* x, const void* y, void* z,
                             unsigned char* ws, cudaStream_t st, void* w);
 
+// The low-workspace schedule (hc_lowmem.cu): the top r axes leaf by leaf.
+struct LowPlan {
+  int D, r;
+  hc_dtype dtype;
+  FwdPlan leaf;  // the plan every leaf of D - r axes runs
+  int n_top;
+  int top_d0[6], top_k[6];
+  int cols_top;
+  size_t off_xl, off_yl, off_leaf;
+  size_t ws_bytes;
+  bool ok;  // false: r outside 1..6, D - r < 1, or a float-float dtype
+};
+LowPlan make_lowmem_plan(int D, hc_dtype dt, int r, int c_req, int kmax_req, int cols,
+                         int cols_outer);
+cudaError_t lowmem_dispatch(const LowPlan& p, const void* x, const void* y, void* z,
+                            unsigned char* ws, cudaStream_t st, void* w);
+
 // c_req, kmax_req <= 0 select the defaults (largest tile, 6 axes per pass).
 FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);
 

@@ -206,3 +206,24 @@ def test_carryfree_arguments_caught_on_host(L):
     assert cf(x, y, x + 16, N, _lib.HC_INT64, ws, nb, None) == _lib.HC_ERR_ALIAS
     assert cf(x, y, z, N, _lib.HC_INT64, z, nb, None) == _lib.HC_ERR_ALIAS
     assert cf(x, y, z, N, _lib.HC_INT64, y - 256, nb, None) == _lib.HC_ERR_ALIAS
+
+
+def test_lowmem_workspace_is_small(L):
+    """The low-workspace schedule needs the two leaf inputs and one leaf's
+    workspace: at D = 20 int64 with 6 top axes, inputs of 2^14 elements and a
+    14-axis leaf's operands -- a few MB against the 2.2 GB of the whole-array
+    passes."""
+    s = _lib.hc_schedule(_lib.HC_SCHED_LOWMEM, 8, 6, 16, 32, 6)
+    low = L.hc_workspace_size_schedule(20, _lib.HC_INT64, ctypes.byref(s))
+    p = _lib.hc_schedule(_lib.HC_SCHED_PASSES, 8, 6, 16, 32, 0)
+    passes = L.hc_workspace_size_schedule(20, _lib.HC_INT64, ctypes.byref(p))
+    assert 0 < low < 8 << 20 and passes > 2 * 3 ** 12 * 2 ** 8 * 8
+    # D = 22: leaves of 16 axes, still a small fraction of the passes' need
+    assert L.hc_workspace_size_schedule(22, _lib.HC_INT64, ctypes.byref(s)) * 50 < \
+        L.hc_workspace_size_schedule(22, _lib.HC_INT64, ctypes.byref(p))
+    # not for the float-float dtypes, and not when no axis is left below
+    assert L.hc_workspace_size_schedule(20, _lib.HC_FP32_MIXED, ctypes.byref(s)) == 0
+    x, y, z, ws = FAKE, FAKE + (1 << 20), FAKE + (1 << 24), FAKE + (1 << 30)
+    bad = _lib.hc_schedule(_lib.HC_SCHED_LOWMEM, 8, 6, 16, 32, 6)
+    assert L.hc_convolve_schedule(x, y, z, 6, _lib.HC_INT64, ctypes.byref(bad), ws, 1 << 20,
+                                  None) == _lib.HC_ERR_ARG

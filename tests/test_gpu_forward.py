@@ -115,6 +115,29 @@ def test_ff_every_schedule(hc, sched):
     assert_bit_equal(gpu_conv(hc, x, y, mixed="ff", **sched), oracle.convolve_ff(x, y))
 
 
+def test_ff_final_stores_into_host_memory(hc):
+    """hc_convolve_out with the float-float dtype: the intermediate stays in
+    the workspace (w must be NULL) and the last pass rounds straight into a
+    page-locked host z; bitwise the oracle."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib as L
+    D = 14
+    x, y = inputs.uniform01_pair(D, seed=1414)
+    lib = L.lib()
+    nb = int(lib.hc_workspace_size(D, L.HC_FP32_FF))
+    ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+    zh = torch.empty(3 ** D, dtype=torch.float32, pin_memory=True)
+    xd, yd = T(x), T(y)
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), xd.data_ptr(), zh.data_ptr(), D,
+                               L.HC_FP32_FF, ws.data_ptr(), nb, st) == L.HC_ERR_ARG
+    assert lib.hc_convolve_out(xd.data_ptr(), yd.data_ptr(), None, zh.data_ptr(), D,
+                               L.HC_FP32_FF, ws.data_ptr(), nb, st) == L.HC_OK
+    torch.cuda.synchronize()
+    assert_bit_equal(zh.numpy(), oracle.convolve_ff(x, y))
+
+
 def test_ff_integer_inputs_rounded_exact(hc):
     """Integer inputs (values in [-2000, 2000], D = 12): the float-float form
     returns the exact result rounded once to binary32 at every output."""
@@ -250,6 +273,24 @@ def test_hybrid_bit_exact(hc, dt, D, top, c, kmax):
         assert_bit_equal(got, oracle.convolve(x, y, threads=8))
 
 
+@pytest.mark.parametrize("dt", [np.int64, np.float64, np.float32])
+@pytest.mark.parametrize("D,top,c,kmax,cols", [(7, 1, 8, 6, 32), (10, 3, 5, 2, 16),
+                                               (13, 6, 4, 3, -32), (15, 2, 8, 6, 8),
+                                               (14, 6, 8, 6, 32), (12, 6, 6, 0, 0)])
+def test_lowmem_bit_exact(hc, dt, D, top, c, kmax, cols):
+    """Low-workspace schedule (the top axes split leaf by leaf): the same bits
+    as the recurrence in every dtype -- leaves of one tile (D - top <= c),
+    of several passes, up to 2^6 sub-cubes summed per leaf element, and a
+    16-byte row-copy width, which the leaves' unaligned slices replace by
+    per-element copies."""
+    if dt is np.int64:
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=800 + D + top)
+    else:
+        x, y = inputs.normal_pair(D, seed=800 + D + top, dtype=dt)
+    got = gpu_conv(hc, x, y, top=top, lowmem=True, c=c, kmax=kmax, cols=cols)
+    assert_bit_equal(got, oracle.convolve(x, y, threads=8))
+
+
 def test_hybrid_d18_float32_workload(hc):
     """The D = 18 float32 workload with 3 direct axes (one 6-axis middle
     pass).  A slice whose top digits hold no 1 has a single sub-cube pair, so
@@ -382,20 +423,24 @@ def test_d16_fp64_separable_closed_form(hc):
     assert np.all(np.abs(z - z_closed) <= bound)
 
 
-@pytest.mark.parametrize("D,bulk", [(17, False), (18, False), (19, False), (20, False),
-                                    (18, True), (20, True)])
-def test_int64_full_size(hc, D, bulk):
+@pytest.mark.parametrize("D,sched", [(17, None), (18, None), (19, None), (20, None),
+                                     (18, "bulk"), (20, "bulk"), (20, "lowmem")])
+def test_int64_full_size(hc, D, sched):
     """D = 17..20 int64, values in [-1000, 1000] (the benchmark workload and
     its sweep, with the tuned schedule of each D, the launch configuration
     the benchmark times): 3^D outputs, 27.9 GB at D = 20.  Checked on whole
     slices (four prefix digits fixed, the oracle's (D-4)-D recurrence on the
     matching sub-cube pairs, summed over the pairs of the digit-1 axes), on
     random single outputs (the definition), and on the sum invariant over all
-    outputs.  bulk: the chunked-bulk schedule (8-axis tiles, 6 middle axes
-    per L2-resident unit, one outer pass) instead of the tuned default."""
+    outputs.  sched "bulk": the chunked-bulk schedule (8-axis tiles, 6 middle
+    axes per L2-resident unit, one outer pass); "lowmem": the low-workspace
+    schedule (6 top axes leaf by leaf, leaves of 14 axes); None: the tuned
+    default."""
     x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2000 + D)
     xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
-    z = hc.convolve(xt, yt, **({'c': 8, 'm': 6, 'bulk': True, 'cols': 32} if bulk else {}))
+    kw = {"bulk": dict(c=8, m=6, bulk=True, cols=32),
+          "lowmem": dict(top=6, lowmem=True, c=8, kmax=6, cols=16, cols_outer=32)}.get(sched, {})
+    z = hc.convolve(xt, yt, **kw)
     torch.cuda.synchronize()
     # sum invariant (no overflow: |sum z| <= (2^20 * 1000)^2)
     assert int(z.sum().item()) == int(x.sum()) * int(y.sum())

@@ -54,6 +54,7 @@ CASES = [
     (_lib.HC_FP64, torch.float64, 13, 15),
     (_lib.HC_FP32, torch.float32, 17, 11),
     (_lib.HC_FP32_MIXED, torch.float32, 13, 12),
+    (_lib.HC_FP32_FF, torch.float32, 12, 13),
 ]
 
 
@@ -80,7 +81,12 @@ def test_no_alloc_matches_hc_convolve_on_two_calls_in_a_row(L, oracle, code, tdt
         assert np.array_equal(g.view(view), w.view(view))
     # the first call against the oracle in the same arithmetic
     x, y = hosts[0]
-    ref = oracle.convolve_mixed(x, y) if code == _lib.HC_FP32_MIXED else oracle.convolve(x, y)
+    if code == _lib.HC_FP32_MIXED:
+        ref = oracle.convolve_mixed(x, y)
+    elif code == _lib.HC_FP32_FF:
+        ref = oracle.convolve_ff(x, y)
+    else:
+        ref = oracle.convolve(x, y)
     g = outs[0][0].cpu().numpy()
     view = np.uint64 if g.itemsize == 8 else np.uint32
     assert np.array_equal(g.view(view), ref.view(view))
