@@ -640,8 +640,13 @@ static cudaError_t run_backward(const BwdPlan& p, const void* dz, const void* x,
     const int d0 = p.it_d0[i], k = p.it_k[i];
     const long long hi = (long long)pow3z(d0);
     const long long lo = (long long)pow3z(a - d0 - k) * (long long)pow3z(C);
-    // the pass over the outermost axes (d0 = 0) takes the outer width
-    const int cols = d0 == 0 && p.n_it >= 2 && fs.cols_outer ? fs.cols_outer : fs.cols;
+    // the pass over the outermost axes (d0 = 0) takes the outer width.  A
+    // 16-column tile of 16-byte row copies over 4-byte elements widens each
+    // row to 20 elements (1.25x the reads); the transposed passes take the
+    // 32-column form instead (D = 18 float32, one GB300: I^T passes 1.605 ->
+    // 1.507 ms, same bits)
+    int cols = d0 == 0 && p.n_it >= 2 && fs.cols_outer ? fs.cols_outer : fs.cols;
+    if (cols == -16 && sizeof(W) == 4) cols = -32;
     e = launch_interp<M, false, true>(k, cols, G, Gbuf, hi, lo, st);
     if (e != cudaSuccess) return e;
     G = Gbuf;
