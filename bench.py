@@ -193,7 +193,7 @@ class Workload:
     """Device-resident inputs, a step function and the bookkeeping for one
     workload."""
 
-    def __init__(self, name, dev, rank=0, D_override=None):
+    def __init__(self, name, dev, rank=0, D_override=None, instances=4096):
         import numpy as np
         import torch
 
@@ -228,7 +228,7 @@ class Workload:
                          mixed={"d16_mixed": True, "d16_ff": "ff"}.get(name, False))
             self.dtype = _dtype_name(name)
         elif name == "batched":
-            dims = inputs.batched_dims(4096, 6, 14, seed)
+            dims = inputs.batched_dims(instances, 6, 14, seed)
             pairs = inputs.batched_uniform01(dims, seed + 1)
             self.dims = [int(d) for d in dims]
             self.host_pairs = pairs
@@ -878,6 +878,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the D=14..19 sweep and the forms after the D=20 headline")
+    ap.add_argument("--instances", type=int, default=4096,
+                    help="instances of the batched workload (4096; smaller batches are for "
+                         "profiling captures)")
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
@@ -913,7 +916,9 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    wl = Workload(args.workload, dev, rank, args.D)
+    if args.instances != 4096 and args.workload != "batched":
+        ap.error("--instances applies to the batched workload only")
+    wl = Workload(args.workload, dev, rank, args.D, args.instances)
     if args.schedule:
         if args.workload not in SINGLE:
             ap.error("--schedule applies to single-instance workloads only")
@@ -971,6 +976,8 @@ def main():
         line["e2e"] = _e2e(wl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(args.workload)
+    if args.instances != 4096:
+        line["config"]["workload"] += f" with {args.instances} instances"
     headline_default = (args.workload == "d20_int64" and args.D is None and not args.schedule)
     if world == 1 and headline_default and not args.no_sweep:
         del wl

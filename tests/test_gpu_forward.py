@@ -587,6 +587,39 @@ def test_convolve_out_device_arrays_and_argument_checks(hc):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("kind,top", [("hybrid", 3), ("lowmem", 4), ("bulk", 0)])
+def test_convolve_out_with_each_int64_default(hc, kind, top):
+    """hc_convolve_out runs the default schedule: with each of the hybrid,
+    low-workspace and chunked-bulk schedules installed as the int64 default,
+    the intermediate goes to w and only the final stores reach a page-locked
+    host z; the oracle's bits, and the default is put back afterwards."""
+    import ctypes
+
+    from paper_1608_00206_gb300 import _lib
+    lib = _lib.lib()
+    D = 13
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=31 + top)
+    hc.convolve(T(x[:2]), T(y[:2]))  # the tuned table is installed first
+    saved = _lib.hc_schedule()
+    assert lib.hc_get_default_schedule(D, _lib.HC_INT64, ctypes.byref(saved)) == 0
+    s = {"hybrid": _lib.hc_schedule(_lib.HC_SCHED_HYBRID, 6, 6, 16, 0, top),
+         "lowmem": _lib.hc_schedule(_lib.HC_SCHED_LOWMEM, 5, 2, 16, 32, top),
+         "bulk": _lib.hc_schedule(_lib.HC_SCHED_CHUNKED_BULK, 7, 4, 16, 0, 0)}[kind]
+    assert lib.hc_set_default_schedule(D, _lib.HC_INT64, ctypes.byref(s)) == 0
+    try:
+        nb = int(lib.hc_workspace_size(D, _lib.HC_INT64))
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=DEV)
+        w = torch.empty(3 ** D, dtype=torch.int64, device=DEV)
+        zh = torch.empty(3 ** D, dtype=torch.int64, pin_memory=True)
+        st = torch.cuda.current_stream().cuda_stream
+        assert lib.hc_convolve_out(T(x).data_ptr(), T(y).data_ptr(), w.data_ptr(),
+                                   zh.data_ptr(), D, _lib.HC_INT64, ws.data_ptr(), nb, st) == 0
+        torch.cuda.synchronize()
+        assert_bit_equal(zh.numpy(), oracle.convolve(x, y, threads=8))
+    finally:
+        assert lib.hc_set_default_schedule(D, _lib.HC_INT64, ctypes.byref(saved)) == 0
+
+
 def _cudart():
     import ctypes
     import glob
