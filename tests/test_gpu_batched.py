@@ -110,6 +110,13 @@ def test_batched_autotune_picks_a_depth(hc):
     for o, r in zip(outs, ref.launch()):
         assert torch.equal(o.view(torch.int32), r.view(torch.int32))
     assert b.status() == 0
+    # and the tuned batch against the oracle on a subset covering every D
+    seen = set()
+    for o, (x, y), d in zip(outs, pairs, dims):
+        if d not in seen:
+            seen.add(d)
+            want = oracle.convolve(x, y)
+            assert np.array_equal(o.cpu().numpy().reshape(-1).view(np.uint32), want.view(np.uint32))
 
 
 def test_bounded_wait_reports_timeout(hc):
