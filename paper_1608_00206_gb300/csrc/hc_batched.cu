@@ -434,7 +434,8 @@ static cudaError_t launch_group_interp_k(const GroupPtrs* tab, int n, long long 
   // columns per tile: 32, except 16 for 8-byte intermediates below 6 axes
   // (two 16-column buffers double-buffer at two CTAs per SM) and 64 for
   // 4-byte ones over 4 axes (81-row tiles: 32 columns leave each CTA only
-  // 10 KB in flight; the 4096-instance float32 batch 9.60 -> 9.47 ms)
+  // 10 KB in flight; the 4096-instance float32 batch 9.60 -> 9.47 ms; 16
+  // columns over 6 axes measured 9.49 -> 10.21 ms and are not used)
   constexpr int L = K1 == 0 ? 256
                     : (sizeof(typename M::W) == 8 && K1 + K2 < 6
                            ? 16

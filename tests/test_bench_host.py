@@ -45,3 +45,53 @@ def test_traffic_lookup_only_on_current_sources(tmp_path, monkeypatch):
     assert bench._traffic_from_profiles("d20_int64", "interp_pass") == pytest.approx(55.0e9)
     assert bench._traffic_from_profiles("d18_fp32", "interp_pass") is None  # other sources
     assert bench._traffic_from_profiles("batched", "batched_interp") is None
+
+
+class _FakeWorkload:
+    """The parts of bench.Workload that the roofline reads."""
+
+    def __init__(self, name, D, alg, bound="hbm"):
+        self.name, self.D, self.D_override = name, D, None
+        self._alg, self._bound = alg, bound
+
+    def kernel_alg(self, kname, launches_per_step):
+        return self._alg / launches_per_step, self._bound
+
+
+def test_roofline_of_the_dominant_kernel(monkeypatch):
+    """The kernel with the largest traced time is the dominant one; achieved
+    = its algorithmic bytes per launch over its mean launch time, against the
+    measured HBM peak."""
+    monkeypatch.setattr(bench, "_peaks", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "_traffic_from_profiles", lambda w, k: None)
+    wl = _FakeWorkload("d20_int64", 20, alg=2 * 60e9)  # per step, two launches
+    prof = {"interp_pass": (20, 200.0), "tile_conv": (10, 60.0)}  # (launches, total ms)
+    r = bench._roofline(wl, prof, steps=10)
+    assert r["kernel"] == "interp_pass" and r["bound"] == "hbm"
+    assert r["ms_per_launch"] == pytest.approx(10.0)
+    assert r["achieved"] == pytest.approx(60e9 / 10e-3 / 1e9)  # GB/s
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
+    assert bench._roofline(wl, {}, steps=10) is None
+
+
+def test_roofline_alu_bound_takes_the_measured_fp64_rate(monkeypatch):
+    monkeypatch.setattr(bench, "_fp64_peak", lambda: (0.5e12, "measured probe"))
+    wl = _FakeWorkload("d16_fp64", 16, alg=3e9, bound="alu")
+    r = bench._roofline(wl, {"tile_conv": (4, 40.0)}, steps=4)
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(0.5)
+    assert r["achieved"] == pytest.approx(3e9 / 10e-3 / 1e12)
+    assert r["frac_of_nominal"] == pytest.approx(r["achieved"] / 0.625)
+
+
+def test_brief_keeps_the_reported_fields():
+    res = {"ms_per_step": 1.23456789, "value": 3.0e11, "alg_hbm_frac": 0.123456,
+           "roofline": {"kernel": "interp_pass", "bound": "hbm", "achieved": 5000.123456,
+                        "frac": 0.7512345, "peak": 6780.7, "unit": "GB/s",
+                        "ms_per_launch": 10.5, "traffic": None, "peak_source": "x"},
+           "kernels": {"interp_pass": {"launches": 2, "ms": 21.0}}, "gpu_launches": 2,
+           "clocks": {"sm_mhz": 2070.0}}
+    b = bench._brief(res)
+    assert b["ms_per_step"] == pytest.approx(1.23457)
+    assert b["dominant"]["kernel"] == "interp_pass" and b["dominant"]["frac"] == 0.7512
+    assert "peak_source" not in b["dominant"]
+    assert b["kernels"] == res["kernels"] and b["clocks"] == res["clocks"]
