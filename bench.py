@@ -324,6 +324,8 @@ class Workload:
             s = _lib.hc_schedule()
             _lib.lib().hc_get_default_schedule(self.D, code, ctypes.byref(s))
             kind, c, k = s.kind, s.c, s.k
+            if kind == 6:
+                kind = 1  # padded whole-array passes: the same geometry
             if kind in (4, 5):  # hybrid / low-workspace defaults (int64)
                 C = min(c or 8, self.D - s.top)
                 if kind == 5:
@@ -884,7 +886,7 @@ def main():
     ap.add_argument("--D", type=int, default=None,
                     help="override D of a single-instance workload (same distribution)")
     ap.add_argument("--schedule", default=None,
-                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|chunked|bulk; "
+                    help="force a schedule kind:c:k:cols[:cols_outer] (kind passes|padded|chunked|bulk; "
                          "hybrid|lowmem:c:k:cols:cols_outer:top) "
                          "instead of the tuned default, e.g. passes:6:6:32")
     args = ap.parse_args()
@@ -923,10 +925,12 @@ def main():
         if args.workload not in SINGLE:
             ap.error("--schedule applies to single-instance workloads only")
         kind, c, k, cols, *outer = args.schedule.split(":")
-        if kind not in ("passes", "chunked", "bulk", "hybrid", "lowmem"):
-            ap.error("schedule kind is passes, chunked, bulk, hybrid or lowmem")
+        if kind not in ("passes", "padded", "chunked", "bulk", "hybrid", "lowmem"):
+            ap.error("schedule kind is passes, padded, chunked, bulk, hybrid or lowmem")
         wl.sched = {"c": int(c), "cols": int(cols),
-                    ("kmax" if kind in ("passes", "hybrid", "lowmem") else "m"): int(k)}
+                    ("kmax" if kind in ("passes", "padded", "hybrid", "lowmem") else "m"): int(k)}
+        if kind == "padded":
+            wl.sched["padded"] = True
         if kind == "bulk":
             wl.sched["bulk"] = True
         if kind in ("hybrid", "lowmem"):

@@ -176,6 +176,18 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
  *                      schedules.  Same bits as every other schedule;
  *                      3^top leaves of about five launches each.  HC_INT64,
  *                      HC_FP64 and HC_FP32 only; HC_ERR_ARG when D <= top.
+ *   HC_SCHED_PADDED  : PASSES with the intermediate kept in the workspace
+ *                      with each tile's 3^c outputs padded to a multiple of
+ *                      128 bytes, so that every row the passes read and write
+ *                      starts on a 128-byte boundary (z's own rows, 3^n
+ *                      elements apart, start at every 8-byte offset); the
+ *                      pass over the outermost axes writes z's layout.  The
+ *                      workspace then holds 3^(D-c) padded tiles (about the
+ *                      size of z) besides the PASSES operands.  Same bits.
+ *                      Measured on GB300 it loses to PASSES (the aligned
+ *                      inner pass gains 15%, the last pass, out of place
+ *                      into z's unaligned rows, takes more than twice as
+ *                      long), so the autotuner does not offer it.
  *   HC_SCHED_DEFAULT : the per-(D, dtype) default (built in: CHUNKED with
  *                      default sizes; replaced by hc_set_default_schedule,
  *                      typically with hc_autotune's winner).
@@ -194,6 +206,7 @@ hc_status hc_convolve(const void* x, const void* y, void* z, int D, hc_dtype dty
 #define HC_SCHED_CHUNKED_BULK 3
 #define HC_SCHED_HYBRID 4
 #define HC_SCHED_LOWMEM 5
+#define HC_SCHED_PADDED 6
 
 typedef struct {
   int kind;

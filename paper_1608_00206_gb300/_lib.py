@@ -20,7 +20,7 @@ _vp, _i, _sz, _cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_cha
 
 
 HC_SCHED_DEFAULT, HC_SCHED_PASSES, HC_SCHED_CHUNKED, HC_SCHED_CHUNKED_BULK = 0, 1, 2, 3
-HC_SCHED_HYBRID, HC_SCHED_LOWMEM = 4, 5
+HC_SCHED_HYBRID, HC_SCHED_LOWMEM, HC_SCHED_PADDED = 4, 5, 6
 
 
 class hc_schedule(ctypes.Structure):

@@ -56,7 +56,7 @@ def _out_shape(x: torch.Tensor, D: int):
 
 
 def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: int = 0,
-              bulk: bool = False, top: int = 0, lowmem: bool = False):
+              bulk: bool = False, top: int = 0, lowmem: bool = False, padded: bool = False):
     """None for the default schedule; else an hc_schedule: top > 0 selects the
     hybrid schedule (direct form on the top axes, c tile axes, kmax axes per
     pass); m > 0 the chunked schedule (c tile axes, m middle axes; bulk=True
@@ -69,7 +69,8 @@ def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: 
         kind = _lib.HC_SCHED_CHUNKED_BULK if bulk else _lib.HC_SCHED_CHUNKED
         return _lib.hc_schedule(kind, c, m, cols, cols_outer)
     if c or kmax:
-        return _lib.hc_schedule(_lib.HC_SCHED_PASSES, c, kmax, cols, cols_outer)
+        kind = _lib.HC_SCHED_PADDED if padded else _lib.HC_SCHED_PASSES
+        return _lib.hc_schedule(kind, c, kmax, cols, cols_outer)
     if cols or cols_outer:
         return _lib.hc_schedule(_lib.HC_SCHED_DEFAULT, 0, 0, cols, cols_outer)
     return None
@@ -78,9 +79,9 @@ def _schedule(c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0, cols_outer: 
 def workspace_size(D: int, dtype: torch.dtype = torch.float32, mixed: bool = False,
                    c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0,
                    cols_outer: int = 0, bulk: bool = False, top: int = 0,
-                   lowmem: bool = False) -> int:
+                   lowmem: bool = False, padded: bool = False) -> int:
     code = _code(dtype, mixed)
-    s = _schedule(c, kmax, m, cols, cols_outer, bulk, top, lowmem)
+    s = _schedule(c, kmax, m, cols, cols_outer, bulk, top, lowmem, padded)
     if s is None:
         # the default schedule is the tuned one once the table is installed
         if torch.cuda.is_available():
@@ -132,7 +133,7 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
              mixed: bool = False, workspace: torch.Tensor | None = None, stream=None,
              c: int = 0, kmax: int = 0, m: int = 0, cols: int = 0,
              cols_outer: int = 0, bulk: bool = False, top: int = 0,
-             lowmem: bool = False) -> torch.Tensor:
+             lowmem: bool = False, padded: bool = False) -> torch.Tensor:
     """z = x * y over {0,1,2}^D.
 
     mixed: False (the inputs' own arithmetic), True (float32 evaluation and
@@ -145,6 +146,7 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
     chunked-bulk variant); top > 0 the hybrid schedule with that many
     direct-form top axes (with lowmem=True: the low-workspace schedule
     splitting that many top axes leaf by leaf); otherwise c or kmax
+    (padded=True: the whole-array passes over a padded, aligned intermediate)
     select the whole-array-pass schedule; cols sets the interpolation tile
     width (cols_outer: that of the pass over the outermost axes).  CPU
     tensors (the end-to-end path): x and y are copied to
@@ -158,7 +160,7 @@ def convolve(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, 
         raise ValueError("x and y must have the same dtype and size")
     D = dim_of(x)
     code = _code(x.dtype, mixed)
-    sched = _schedule(c, kmax, m, cols, cols_outer, bulk, top, lowmem)
+    sched = _schedule(c, kmax, m, cols, cols_outer, bulk, top, lowmem, padded)
     if x.is_cuda:
         if not y.is_cuda or y.device != x.device:
             raise ValueError("x and y must be on the same CUDA device")

@@ -31,10 +31,13 @@ namespace hc {
 // ---------------------------------------------------------------------------
 // K2 kernel: one tile per outer index alpha (grid-stride over tiles).
 
+// pitch: elements between consecutive tiles' outputs (3^C, or more for the
+// padded intermediate of HC_SCHED_PADDED).
 template <class M, int C, bool FINAL>
 __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __restrict__ X,
                                                         const typename M::In* __restrict__ Y,
-                                                        void* __restrict__ out_, long long ntiles) {
+                                                        void* __restrict__ out_, long long ntiles,
+                                                        long long pitch) {
   typedef typename M::In In;
   typedef typename std::conditional<FINAL, typename M::Out, typename M::W>::type O;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __
     }
     __syncthreads();  // this tile's rows are in buffer `it`
     RowLoader<In> ld{rows + (it * 2 + 0) * p2(C), rows + (it * 2 + 1) * p2(C)};
-    tile_body<M, C, FINAL>(ld, reinterpret_cast<O*>(out_) + t * p3(C), smem);
+    tile_body<M, C, FINAL>(ld, reinterpret_cast<O*>(out_) + t * pitch, smem);
     if constexpr (TileShape<C>::G == 1) __syncthreads();  // buffer reuse (larger tiles end with one)
   }
 }
@@ -70,11 +73,11 @@ template <class M, int C>
 __global__ void __launch_bounds__(256) tile_conv_bulk_kernel(const typename M::In* __restrict__ X,
                                                              const typename M::In* __restrict__ Y,
                                                              typename M::W* __restrict__ out,
-                                                             long long ntiles) {
+                                                             long long ntiles, long long pitch) {
   typedef typename M::In In;
   extern __shared__ __align__(16) unsigned char smem[];
   tile_loop_bulk<M, C>([&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); },
-                       [&](long long t) { return out + t * p3(C); }, ntiles, smem);
+                       [&](long long t) { return out + t * pitch; }, ntiles, smem);
 }
 
 // HC_FP32_FF: the binary32 inputs as float-float pairs (x, 0), written once
@@ -110,7 +113,7 @@ static int threads_for_tile(int C) { return C >= 4 ? 256 : 32; }
 
 template <class M, int C, bool FINAL>
 static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* Y, void* out,
-                                 long long ntiles, cudaStream_t st) {
+                                 long long ntiles, cudaStream_t st, long long pitch) {
   ProfileScope prof(st, "tile_conv");
   if constexpr (use_bulk_tiles<M, C, FINAL>()) {
     if (is_device_allocation(out)) {
@@ -118,7 +121,8 @@ static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* 
       auto k = tile_conv_bulk_kernel<M, C>;
       cudaError_t e = prep_kernel(k, smem);
       if (e != cudaSuccess) return e;
-      k<<<grid_for(k, 256, smem, ntiles), 256, smem, st>>>(X, Y, (typename M::W*)out, ntiles);
+      k<<<grid_for(k, 256, smem, ntiles), 256, smem, st>>>(X, Y, (typename M::W*)out, ntiles,
+                                                           pitch);
       return cudaGetLastError();
     }
   }
@@ -127,31 +131,32 @@ static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* 
   cudaError_t e = prep_kernel(k, smem);
   if (e != cudaSuccess) return e;
   const int threads = threads_for_tile(C);
-  k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(X, Y, out, ntiles);
+  k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(X, Y, out, ntiles, pitch);
   return cudaGetLastError();
 }
 
 template <class M, bool FINAL>
 static cudaError_t launch_tile(int C, const typename M::In* X, const typename M::In* Y, void* out,
-                               long long ntiles, cudaStream_t st) {
+                               long long ntiles, cudaStream_t st, long long pitch = 0) {
+  if (pitch == 0) pitch = (long long)pow3z(C);
   switch (C) {
-    case 1: return launch_tile_c<M, 1, FINAL>(X, Y, out, ntiles, st);
-    case 2: return launch_tile_c<M, 2, FINAL>(X, Y, out, ntiles, st);
-    case 3: return launch_tile_c<M, 3, FINAL>(X, Y, out, ntiles, st);
-    case 4: return launch_tile_c<M, 4, FINAL>(X, Y, out, ntiles, st);
-    case 5: return launch_tile_c<M, 5, FINAL>(X, Y, out, ntiles, st);
-    case 6: return launch_tile_c<M, 6, FINAL>(X, Y, out, ntiles, st);
-    case 7: return launch_tile_c<M, 7, FINAL>(X, Y, out, ntiles, st);
-    case 8: return launch_tile_c<M, 8, FINAL>(X, Y, out, ntiles, st);
+    case 1: return launch_tile_c<M, 1, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 2: return launch_tile_c<M, 2, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 3: return launch_tile_c<M, 3, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 4: return launch_tile_c<M, 4, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 5: return launch_tile_c<M, 5, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 6: return launch_tile_c<M, 6, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 7: return launch_tile_c<M, 7, FINAL>(X, Y, out, ntiles, st, pitch);
+    case 8: return launch_tile_c<M, 8, FINAL>(X, Y, out, ntiles, st, pitch);
     case 9:
-      if constexpr (sizeof(typename M::W) == 4) return launch_tile_c<M, 9, FINAL>(X, Y, out, ntiles, st);
+      if constexpr (sizeof(typename M::W) == 4) return launch_tile_c<M, 9, FINAL>(X, Y, out, ntiles, st, pitch);
       return cudaErrorInvalidValue;
   }
   return cudaErrorInvalidValue;
 }
 
 // The plan: which axes go where, and the workspace layout.
-FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req) {
+FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req, bool padded) {
   FwdPlan p;
   memset(&p, 0, sizeof(p));
   p.D = D;
@@ -206,7 +211,16 @@ FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req) {
   p.off_ty = off;
   off = align_up(off + tmax * in_sz, 256);
   p.off_w = off;
-  if (wide_intermediate(dt) && p.a > 0) off = align_up(off + pow3z(D) * w_sz, 256);
+  p.padded = padded && p.a > 0;
+  if (p.padded) {
+    // tile pitch: 3^C rounded up to 128 bytes of intermediate elements
+    const long long q = (long long)(128 / w_sz);
+    p.pitch = ((long long)pow3z(C) + q - 1) / q * q;
+    off = align_up(off + pow3z(p.a) * (size_t)p.pitch * w_sz, 256);
+  } else {
+    p.pitch = (long long)pow3z(C);
+    if (wide_intermediate(dt) && p.a > 0) off = align_up(off + pow3z(D) * w_sz, 256);
+  }
   p.ws_bytes = off;
   return p;
 }
@@ -243,6 +257,27 @@ static cudaError_t run_forward(const FwdPlan& p, const void* x, const void* y, v
   }
   // K2
   const long long ntiles = (long long)pow3z(a);
+  if (p.padded) {
+    // the intermediate in the workspace, tile t at t * pitch (every row of
+    // every pass 128-byte aligned); the last pass writes z's own layout
+    W* Pw = (W*)(ws + p.off_w);
+    e = launch_tile<M, false>(C, X, Y, Pw, ntiles, st, p.pitch);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < p.n_interp; ++i) {
+      const int d0 = p.interp_d0[i], k = p.interp_k[i];
+      const long long hi = (long long)pow3z(d0);
+      const long long lo = (long long)pow3z(a - d0 - k) * p.pitch;
+      const bool last = (i == p.n_interp - 1);  // d0 = 0: the outermost axes, hi = 1
+      const int cols = last && p.cols_outer ? p.cols_outer : p.cols;
+      if (last)
+        e = launch_interp_remap<M>(k, cols, Pw, (typename M::Out*)z, lo, p.pitch,
+                                   (long long)pow3z(C), st);
+      else
+        e = launch_interp<M, false>(k, cols, Pw, Pw, hi, lo, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   const bool mixed_ws = (sizeof(W) != sizeof(typename M::Out)) && a > 0;
   // split: the caller's array holds the intermediate, z only the final stores
   const bool split = !mixed_ws && w_user != nullptr && sizeof(W) == sizeof(typename M::Out);
@@ -389,7 +424,7 @@ static bool g_has_default[HC_MAX_D + 1][kNumDtypes];
 
 bool schedule_valid(const hc_schedule& s, hc_dtype dtype) {
   const int cmax = dtype == HC_FP32 ? 9 : 8;
-  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_LOWMEM) return false;
+  if (s.kind < HC_SCHED_DEFAULT || s.kind > HC_SCHED_PADDED) return false;
   if (s.c < 0 || s.c > cmax || s.k < 0 || s.k > 6) return false;
   if (s.kind == HC_SCHED_HYBRID) {
     if (s.top < 1 || s.top > 6 || s.c > 8 || !hybrid_dtype_ok(dtype)) return false;
@@ -419,7 +454,7 @@ hc_schedule resolve_schedule(int D, hc_dtype dtype, const hc_schedule* s) {
 }
 
 static FwdPlan passes_plan(int D, hc_dtype dt, const hc_schedule& s) {
-  FwdPlan p = make_fwd_plan(D, dt, s.c, s.k);
+  FwdPlan p = make_fwd_plan(D, dt, s.c, s.k, s.kind == HC_SCHED_PADDED);
   p.cols = s.cols;
   p.cols_outer = s.cols_outer;
   return p;
@@ -450,7 +485,8 @@ static LowPlan lowmem_plan(int D, hc_dtype dt, const hc_schedule& s) {
 }
 
 static size_t plan_ws(int D, hc_dtype dtype, const hc_schedule& s) {
-  if (s.kind == HC_SCHED_PASSES || D == 0) return passes_plan(D, dtype, s).ws_bytes;
+  if (s.kind == HC_SCHED_PASSES || s.kind == HC_SCHED_PADDED || D == 0)
+    return passes_plan(D, dtype, s).ws_bytes;
   if (s.kind == HC_SCHED_LOWMEM) {
     const LowPlan l = lowmem_plan(D, dtype, s);
     return l.ok ? l.ws_bytes : 0;
@@ -516,7 +552,7 @@ hc_status convolve_checked(const void* x, const void* y, void* z, int D, hc_dtyp
     x = xw;
     y = yw;
   }
-  if (s.kind == HC_SCHED_PASSES || D == 0)
+  if (s.kind == HC_SCHED_PASSES || s.kind == HC_SCHED_PADDED || D == 0)
     return record_cuda_error(forward_dispatch(passes_plan(D, dtype, s), x, y, z,
                                               (unsigned char*)workspace, stream, w));
   if (s.kind == HC_SCHED_HYBRID)

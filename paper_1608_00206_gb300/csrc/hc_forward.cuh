@@ -19,6 +19,11 @@ struct FwdPlan {
   size_t ws_bytes;
   int cols;        // columns per whole-array interpolation tile (0 = default)
   int cols_outer;  // the same for the pass over the outermost axes (0 = cols)
+  // HC_SCHED_PADDED: the intermediate in the workspace with a 128-byte tile
+  // pitch (off_w, 3^a * pitch elements), so that every row of the passes is
+  // aligned; the last pass writes z's own layout
+  bool padded;
+  long long pitch;
 };
 
 // The default schedule ("chunked"): the a' = D - C - m outermost axes are
@@ -99,7 +104,7 @@ cudaError_t lowmem_dispatch(const LowPlan& p, const void* x, const void* y, void
                             unsigned char* ws, cudaStream_t st, void* w);
 
 // c_req, kmax_req <= 0 select the defaults (largest tile, 6 axes per pass).
-FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req);
+FwdPlan make_fwd_plan(int D, hc_dtype dt, int c_req, int kmax_req, bool padded = false);
 
 cudaError_t forward_dispatch(const FwdPlan& p, const void* x, const void* y, void* z,
                              unsigned char* ws, cudaStream_t st, void* w = nullptr);

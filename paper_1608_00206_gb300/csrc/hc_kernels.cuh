@@ -235,6 +235,125 @@ inline cudaError_t launch_interp_k(int cols, const typename M::W* src, void* dst
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// The last pass of the padded schedule: interpolate the k outermost axes of
+// the padded intermediate [3^k][lo] (lo = 3^(a-k) * pitch: blocks of `pitch`
+// columns of which the first cn = 3^C are real) and store the results in z's
+// own layout [3^k][lo / pitch * cn].  The reads are 128-byte aligned rows;
+// padding columns are read and interpolated but never stored.  K1 > 0: one
+// round-1 pencil per thread prefetched into registers for the next tile
+// while round 2 of this one runs (as interp_tiles_regpipe); K1 == 0: whole
+// columns per thread, no shared memory.
+template <class M, int K1, int K2, int L>
+__global__ void __launch_bounds__(K1 > 0 ? p3(K2) * L : 256)
+    interp_remap_kernel(const typename M::W* __restrict__ src, typename M::Out* __restrict__ dst,
+                        long long lo, long long pitch, long long cn) {
+  typedef typename M::W W;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const long long lo_z = lo / pitch * cn;
+  auto zcol = [&](long long c, long long& zc) -> bool {  // false: a padding column
+    const long long q = c / pitch, r = c - q * pitch;
+    zc = q * cn + r;
+    return c < lo && r < cn;
+  };
+  if constexpr (K1 == 0) {
+#pragma unroll 1
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < lo;
+         c += (long long)gridDim.x * blockDim.x) {
+      long long zc;
+      if (!zcol(c, zc)) continue;
+      W v[p3(K2)];
+#pragma unroll
+      for (int j = 0; j < p3(K2); ++j) v[j] = src[j * lo + c];
+      interp_pencil<M, K2>(v);
+#pragma unroll
+      for (int j = 0; j < p3(K2); ++j) dst[j * lo_z + zc] = M::out(v[j]);
+    }
+  } else {
+    W* T = reinterpret_cast<W*>(smem);
+    const long long ntiles = (lo + L - 1) / L;
+    const int tid = threadIdx.x;
+    const int a1 = tid / L, l1 = tid - a1 * L;  // round 1: outer index a1, column l1
+    constexpr int N1 = p3(K1) * L;
+    W pre[p3(K2)];
+    auto fetch = [&](long long t) {
+      const long long c = t * L + l1;
+      if (tid < N1 && c < lo) {
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) pre[j] = src[(long long)(a1 * p3(K2) + j) * lo + c];
+      }
+    };
+    long long t = blockIdx.x;
+    if (t < ntiles) fetch(t);
+#pragma unroll 1
+    for (; t < ntiles; t += gridDim.x) {
+      const long long l0 = t * L;
+      if (tid < N1 && l0 + l1 < lo) {
+        W v[p3(K2)];
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) v[j] = pre[j];
+        interp_pencil<M, K2>(v);
+#pragma unroll
+        for (int j = 0; j < p3(K2); ++j) T[(a1 * p3(K2) + j) * L + l1] = v[j];
+      }
+      __syncthreads();
+      if (t + gridDim.x < ntiles) fetch(t + gridDim.x);
+      {  // round 2: inner index r = tid / L, column l = tid % L (all p3(K2) * L threads)
+        const int r = tid / L, l = tid - r * L;
+        long long zc;
+        if (zcol(l0 + l, zc)) {
+          W v[p3(K1)];
+#pragma unroll
+          for (int j = 0; j < p3(K1); ++j) v[j] = T[(j * p3(K2) + r) * L + l];
+          interp_pencil<M, K1>(v);
+#pragma unroll
+          for (int j = 0; j < p3(K1); ++j)
+            dst[(long long)(j * p3(K2) + r) * lo_z + zc] = M::out(v[j]);
+        }
+      }
+      __syncthreads();  // T is rewritten by the next tile's round 1
+    }
+  }
+}
+
+template <class M, int K1, int K2, int L>
+inline cudaError_t launch_remap_kl(const typename M::W* src, typename M::Out* dst, long long lo,
+                                   long long pitch, long long cn, cudaStream_t st) {
+  auto k = interp_remap_kernel<M, K1, K2, L>;
+  ProfileScope prof(st, "interp_remap");
+  constexpr size_t smem = K1 > 0 ? sizeof(typename M::W) * (size_t)p3(K1 + K2) * L : 0;
+  cudaError_t e = prep_kernel(k, smem);
+  if (e != cudaSuccess) return e;
+  constexpr int threads = K1 > 0 ? p3(K2) * L : 256;
+  const long long work = K1 > 0 ? (lo + L - 1) / L : (lo + 255) / 256;
+  k<<<grid_for(k, threads, smem, work), threads, smem, st>>>(src, dst, lo, pitch, cn);
+  return cudaGetLastError();
+}
+
+// The padded schedule's last pass over k = 1..6 outermost axes; cols: 16 or
+// 32 columns per tile (the sign of a 16-byte-copy width is ignored).
+template <class M>
+inline cudaError_t launch_interp_remap(int k, int cols, const typename M::W* src,
+                                       typename M::Out* dst, long long lo, long long pitch,
+                                       long long cn, cudaStream_t st) {
+  const bool wide = (cols < 0 ? -cols : cols) >= 32;
+  switch (k) {
+    case 1: return launch_remap_kl<M, 0, 1, 256>(src, dst, lo, pitch, cn, st);
+    case 2: return launch_remap_kl<M, 0, 2, 256>(src, dst, lo, pitch, cn, st);
+    case 3: return launch_remap_kl<M, 0, 3, 256>(src, dst, lo, pitch, cn, st);
+    case 4:
+      return wide ? launch_remap_kl<M, 1, 3, 32>(src, dst, lo, pitch, cn, st)
+                  : launch_remap_kl<M, 1, 3, 16>(src, dst, lo, pitch, cn, st);
+    case 5:
+      return wide ? launch_remap_kl<M, 2, 3, 32>(src, dst, lo, pitch, cn, st)
+                  : launch_remap_kl<M, 2, 3, 16>(src, dst, lo, pitch, cn, st);
+    case 6:
+      return wide ? launch_remap_kl<M, 3, 3, 32>(src, dst, lo, pitch, cn, st)
+                  : launch_remap_kl<M, 3, 3, 16>(src, dst, lo, pitch, cn, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // Interpolation (TR = false) or its transpose (TR = true) of k consecutive
 // axes of a [hi][3^k][lo] array, src -> dst (may be the same array).
 template <class M, bool FINAL, bool TR = false>

@@ -273,6 +273,33 @@ def test_hybrid_bit_exact(hc, dt, D, top, c, kmax):
         assert_bit_equal(got, oracle.convolve(x, y, threads=8))
 
 
+@pytest.mark.parametrize("kind", ["int64", "float64", "float32", "mixed", "ff"])
+@pytest.mark.parametrize("D,c,kmax,cols,cols_outer", [(9, 8, 6, 16, 0), (11, 8, 3, 32, 0),
+                                                      (14, 8, 6, 16, 32), (15, 7, 4, -16, 16),
+                                                      (16, 5, 6, -32, 32), (13, 4, 5, 8, -16),
+                                                      (12, 6, 2, 32, 0)])
+def test_padded_every_dtype(hc, kind, D, c, kmax, cols, cols_outer):
+    """Padded schedule (the intermediate with 128-byte-aligned tile pitch in
+    the workspace, the last pass writing z's layout): the recurrence's bits in
+    every dtype -- last passes of 1 to 6 axes (register-only and shared-memory
+    forms, 16 and 32 columns), inner passes with every tile width, tiles
+    whose 3^c outputs are padded by 1 to 31 elements."""
+    if kind == "int64":
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=900 + D + c)
+        want = oracle.convolve(x, y, threads=8)
+    elif kind in ("mixed", "ff"):
+        x, y = inputs.uniform01_pair(D, seed=900 + D + c)
+        want = oracle.convolve_mixed(x, y) if kind == "mixed" else oracle.convolve_ff(x, y)
+    else:
+        x, y = inputs.normal_pair(D, seed=900 + D + c,
+                                  dtype=np.float64 if kind == "float64" else np.float32)
+        want = oracle.convolve(x, y, threads=8)
+    mixed = {"mixed": True, "ff": "ff"}.get(kind, False)
+    got = gpu_conv(hc, x, y, mixed=mixed, padded=True, c=c, kmax=kmax, cols=cols,
+                   cols_outer=cols_outer)
+    assert_bit_equal(got, want)
+
+
 @pytest.mark.parametrize("dt", [np.int64, np.float64, np.float32])
 @pytest.mark.parametrize("D,top,c,kmax,cols", [(7, 1, 8, 6, 32), (10, 3, 5, 2, 16),
                                                (13, 6, 4, 3, -32), (15, 2, 8, 6, 8),
@@ -424,7 +451,8 @@ def test_d16_fp64_separable_closed_form(hc):
 
 
 @pytest.mark.parametrize("D,sched", [(17, None), (18, None), (19, None), (20, None),
-                                     (18, "bulk"), (20, "bulk"), (20, "lowmem")])
+                                     (18, "bulk"), (20, "bulk"), (20, "lowmem"),
+                                     (19, "padded"), (20, "padded")])
 def test_int64_full_size(hc, D, sched):
     """D = 17..20 int64, values in [-1000, 1000] (the benchmark workload and
     its sweep, with the tuned schedule of each D, the launch configuration
@@ -439,7 +467,8 @@ def test_int64_full_size(hc, D, sched):
     x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=2000 + D)
     xt, yt = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
     kw = {"bulk": dict(c=8, m=6, bulk=True, cols=32),
-          "lowmem": dict(top=6, lowmem=True, c=8, kmax=6, cols=16, cols_outer=32)}.get(sched, {})
+          "lowmem": dict(top=6, lowmem=True, c=8, kmax=6, cols=16, cols_outer=32),
+          "padded": dict(padded=True, c=8, kmax=6, cols=16, cols_outer=16)}.get(sched, {})
     z = hc.convolve(xt, yt, **kw)
     torch.cuda.synchronize()
     # sum invariant (no overflow: |sum z| <= (2^20 * 1000)^2)
@@ -587,7 +616,7 @@ def test_convolve_out_device_arrays_and_argument_checks(hc):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("kind,top", [("hybrid", 3), ("lowmem", 4), ("bulk", 0)])
+@pytest.mark.parametrize("kind,top", [("hybrid", 3), ("lowmem", 4), ("bulk", 0), ("padded", 0)])
 def test_convolve_out_with_each_int64_default(hc, kind, top):
     """hc_convolve_out runs the default schedule: with each of the hybrid,
     low-workspace and chunked-bulk schedules installed as the int64 default,
@@ -604,7 +633,8 @@ def test_convolve_out_with_each_int64_default(hc, kind, top):
     assert lib.hc_get_default_schedule(D, _lib.HC_INT64, ctypes.byref(saved)) == 0
     s = {"hybrid": _lib.hc_schedule(_lib.HC_SCHED_HYBRID, 6, 6, 16, 0, top),
          "lowmem": _lib.hc_schedule(_lib.HC_SCHED_LOWMEM, 5, 2, 16, 32, top),
-         "bulk": _lib.hc_schedule(_lib.HC_SCHED_CHUNKED_BULK, 7, 4, 16, 0, 0)}[kind]
+         "bulk": _lib.hc_schedule(_lib.HC_SCHED_CHUNKED_BULK, 7, 4, 16, 0, 0),
+         "padded": _lib.hc_schedule(_lib.HC_SCHED_PADDED, 7, 3, 16, 32, 0)}[kind]
     assert lib.hc_set_default_schedule(D, _lib.HC_INT64, ctypes.byref(s)) == 0
     try:
         nb = int(lib.hc_workspace_size(D, _lib.HC_INT64))
