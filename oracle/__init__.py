@@ -25,6 +25,15 @@ and marshals numpy arrays.  Functions and the passages they follow:
   respect to x and y (transpose of the recurrence; brute-force correlation).
 * :func:`zabs` -- magnitude companion for the forward-error bound
   ``|z_hat - z| <= gamma_{3D+1} * zabs``.
+* :func:`maxconv_brute` -- max-convolution (Discussion, the (x, max)
+  semiring) from its definition, in C++.
+* :func:`maxconv_p`, :func:`maxconv_pnorm`, :func:`maxconv_limb_plan`,
+  :func:`maxconv_limb_sums` -- the Discussion's p-norm route to exact
+  max-convolution of bounded non-negative integers, in Python integers
+  (arbitrary size, exact; small D only): the choice of p, the p-norm
+  estimate rounded to the nearest integer, and the sums of p-th powers
+  recovered from one int64 hypercube convolution whose extra axes are the
+  bits of a limb index (the carry-free embedding of the same Discussion).
 
 Dtype handling: int64 arrays are computed in Z/2^64 (two's complement wrap),
 float64 and float32 in their own precision.
@@ -32,6 +41,7 @@ float64 and float32 in their own precision.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -76,6 +86,7 @@ def _lib():
             lib.oracle_adjoint.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_adjoint_brute.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_zabs.argtypes = [vp, vp, vp, i]
+            lib.oracle_maxconv_brute.argtypes = [vp, vp, vp, i]
             lib.oracle_max_threads.restype = i
             _LIB = lib
     return _LIB
@@ -252,3 +263,157 @@ def gamma(n: int, u: float) -> float:
 
 def max_threads() -> int:
     return int(_lib().oracle_max_threads())
+
+
+# --------------------------------------------------------------------------
+# Max-convolution through p-norm rings (Discussion).
+#
+# For non-negative integers of bounded range, max over a set of N terms u of
+# the products x[i]*y[j] with i + j = k is approximated by the p-norm
+# ||u||_p = (sum u^p)^(1/p), and sum u^p over those pairs is the ordinary
+# convolution of x^p and y^p.  Since max u <= ||u||_p <= N^(1/p) max u, the
+# estimate exceeds the maximum by at most M (N^(1/p) - 1), M the largest
+# possible product; once that is below 1/2, the integer nearest the estimate
+# is the maximum.  Readings: N = 2^D (an output has 2^{#ones(k)} <= 2^D
+# pairs); M = vmax^2 for entries in [0, vmax]; the half unit is kept with a
+# margin of 1/16 (the bound is required to be below 7/16) so that a root
+# extracted in floating point still rounds to the right integer.
+
+def maxconv_brute(x, y) -> np.ndarray:
+    """z[k] = max of x[i]*y[j] over the pairs i + j = k (O(4^D), int64)."""
+    x = np.ascontiguousarray(x, dtype=np.int64).reshape(-1)
+    y = np.ascontiguousarray(y, dtype=np.int64).reshape(-1)
+    if x.size != y.size:
+        raise ValueError("x and y differ in length")
+    D = dim_of(x)
+    z = np.empty(3 ** D, dtype=np.int64)
+    if _lib().oracle_maxconv_brute(_ptr(x), _ptr(y), _ptr(z), D):
+        raise RuntimeError("oracle_maxconv_brute failed")
+    return z
+
+
+def maxconv_bound_holds(D: int, vmax: int, p: int, num: int = 7, den: int = 16) -> bool:
+    """M (2^(D/p) - 1) < num/den with M = vmax^2, decided exactly:
+    2^D (den M)^p < (den M + num)^p in integers."""
+    M = vmax * vmax
+    return (1 << D) * (den * M) ** p < (den * M + num) ** p
+
+
+def maxconv_p(D: int, vmax: int, num: int = 7, den: int = 16) -> int:
+    """The smallest integer p >= 1 for which the p-norm estimate of every
+    output is within num/den of its maximum (default 7/16: the paper's 1/2
+    with a margin of 1/16)."""
+    if vmax < 0 or D < 0:
+        raise ValueError("vmax and D must be non-negative")
+    M = vmax * vmax
+    if M == 0:
+        return 1
+    # Starting guess from logarithms, then exact steps down and up.
+    p = max(1, int(math.ceil(D * math.log(2.0) / math.log1p(num / (den * M)))))
+    while p > 1 and maxconv_bound_holds(D, vmax, p - 1, num, den):
+        p -= 1
+    while not maxconv_bound_holds(D, vmax, p, num, den):
+        p += 1
+    return p
+
+
+def _iroot(s: int, p: int) -> int:
+    """floor(s^(1/p)) for an integer s >= 0 (integer Newton from above)."""
+    if s < 2 or p == 1:
+        return s
+    r = 1 << -(-s.bit_length() // p)
+    while True:
+        q = ((p - 1) * r + s // r ** (p - 1)) // p
+        if q >= r:
+            return r
+        r = q
+
+
+def nearest_root(s: int, p: int) -> int:
+    """The integer nearest s^(1/p) (exact; a tie cannot occur for the sums here
+    but would round up)."""
+    r = _iroot(s, p)
+    return r + 1 if (s << p) >= (2 * r + 1) ** p else r
+
+
+def _pow_sums(x, y, p: int):
+    """s[k] = sum over i + j = k of (x[i] y[j])^p in Python integers
+    (Algorithm 1's pair loop)."""
+    D = dim_of(np.asarray(x).reshape(-1))
+    t = tmap(D).tolist()
+    xp = [int(v) ** p for v in np.asarray(x).reshape(-1).tolist()]
+    yp = [int(v) ** p for v in np.asarray(y).reshape(-1).tolist()]
+    s = [0] * (3 ** D)
+    for i, a in enumerate(xp):
+        if a:
+            ti = t[i]
+            for j, b in enumerate(yp):
+                if b:
+                    s[ti + t[j]] += a * b
+    return s
+
+
+def maxconv_pnorm(x, y, vmax: int, p: int | None = None) -> np.ndarray:
+    """The Discussion's route: the sums of p-th powers (an ordinary hypercube
+    convolution of x^p and y^p), then the integer nearest each p-th root.
+    Entries must lie in [0, vmax]; p defaults to maxconv_p(D, vmax)."""
+    x = np.asarray(x, dtype=np.int64).reshape(-1)
+    y = np.asarray(y, dtype=np.int64).reshape(-1)
+    D = dim_of(x)
+    if x.min(initial=0) < 0 or y.min(initial=0) < 0 or max(x.max(), y.max()) > vmax:
+        raise ValueError("entries outside [0, vmax]")
+    if p is None:
+        p = maxconv_p(D, vmax)
+    return np.array([nearest_root(sk, p) for sk in _pow_sums(x, y, p)], dtype=np.int64)
+
+
+def maxconv_limb_plan(D: int, vmax: int):
+    """(p, b, e, L) for the int64 evaluation of the sums of p-th powers: each
+    vmax^p-sized value is written as L limbs of b bits, and the limb index a
+    (0 <= a < 2^e, L <= 2^e) becomes e extra hypercube axes.  Every entry of
+    the (D + e)-axis int64 convolution, and every sum of its limb-value
+    slices, is below 2^(D + e + 2b) <= 2^63, so Z/2^64 holds it exactly."""
+    p = maxconv_p(D, vmax)
+    bits = max(1, (vmax ** p).bit_length()) if vmax > 1 else 1
+    e = 0
+    while True:
+        b = min(31, (63 - D - e) // 2)
+        if b < 1:
+            raise ValueError("no limb width keeps the sums below 2^63")
+        L = -(-bits // b)
+        if L <= (1 << e):
+            return p, b, e, L
+        e += 1
+
+
+def maxconv_limb_sums(x, y, vmax: int):
+    """(w, b, p): w[c, k] = sum over limb pairs a + a' = c of the convolution of
+    limb a of x^p with limb a' of y^p, so that sum_c w[c, k] 2^(c b) is the
+    sum of p-th powers s[k].  Computed with one int64 recurrence of D + e
+    axes (oracle.convolve) whose top e axes carry the limb index bits: the
+    carry-free digit string of a + a' on those axes, read in base 2, is the
+    value c = a + a'."""
+    x = np.asarray(x, dtype=np.int64).reshape(-1)
+    y = np.asarray(y, dtype=np.int64).reshape(-1)
+    D = dim_of(x)
+    p, b, e, L = maxconv_limb_plan(D, vmax)
+    n = 1 << D
+    mask = (1 << b) - 1
+
+    def limbs(v):
+        U = np.zeros(((1 << e), n), dtype=np.int64)
+        for i, val in enumerate(v.tolist()):
+            w = int(val) ** p
+            for a in range(L):
+                U[a, i] = (w >> (a * b)) & mask
+        return U.reshape(-1)
+
+    W = convolve(limbs(x), limbs(y)).reshape(3 ** e, 3 ** D)
+    w = np.zeros(((2 << e) - 1, 3 ** D), dtype=np.int64)
+    for d in range(3 ** e):
+        c, q = 0, d
+        for j in range(e):           # digit j of d (least significant first) weighs 2^j
+            c += (q % 3) << j
+            q //= 3
+        w[c] += W[d]
+    return w, b, p

@@ -108,6 +108,24 @@ T point(const T* x, const T* y, int D, size_t k) {
   return acc;
 }
 
+// Max-convolution (Discussion: the (x, max) semiring that p-norm rings
+// approximate): every pair (i, j) offers x[i]*y[j] to z[i+j] and z keeps the
+// largest offer.  O(4^D), straight from the definition; every output index
+// is reached (digit 0 by (0,0), 2 by (1,1), 1 by (0,1) and (1,0)), so no
+// output keeps its starting value.  int64 products (the caller keeps
+// |x|, |y| < 2^31).
+void maxconv_brute(const int64_t* x, const int64_t* y, int64_t* z, int D) {
+  const size_t n2 = (size_t)1 << D, n3 = pow3(D);
+  for (size_t k = 0; k < n3; ++k) z[k] = INT64_MIN;
+  std::vector<size_t> t(n2);
+  for (size_t i = 0; i < n2; ++i) t[i] = tmap(i, D);
+  for (size_t i = 0; i < n2; ++i)
+    for (size_t j = 0; j < n2; ++j) {
+      const int64_t v = x[i] * y[j];
+      if (v > z[t[i] + t[j]]) z[t[i] + t[j]] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The Methods recurrence (3-way split), on fresh temporaries:
 //   z[0] = x[0]*y[0];  z[2] = x[1]*y[1];
@@ -624,6 +642,12 @@ int oracle_adjoint_brute(const void* g, const void* x, const void* y, void* dx, 
 int oracle_zabs(const double* absx, const double* absy, double* z, int D) {
   std::vector<double> scratch(((size_t)2 << D) + 2);
   zabs_rec(absx, absy, z, D, scratch.data());
+  return 0;
+}
+
+int oracle_maxconv_brute(const int64_t* x, const int64_t* y, int64_t* z, int D) {
+  if (D < 0 || D > 20) return 1;
+  maxconv_brute(x, y, z, D);
   return 0;
 }
 
