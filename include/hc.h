@@ -292,6 +292,44 @@ hc_status hc_carryfree(const void* x, const void* y, void* z, size_t N, hc_dtype
                        void* workspace, size_t ws_bytes, hc_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Max-convolution of bounded non-negative integers (Discussion: p-norm rings
+ * make max-convolution on hypercubes of integers with bounded dynamic range
+ * exact once p is large enough and the p-norm estimates are rounded to the
+ * nearest integer).  For x, y over {0,1}^D with every entry in [0, vmax]:
+ *     z[k] = max of x[i] * y[j] over the pairs i + j = k,
+ * all int64, same layouts as hc_convolve.  Method: with M = vmax^2 and p the
+ * smallest integer for which M (2^(D/p) - 1) < 7/16 (the paper's error
+ * bound below 1/2, kept 1/16 away from it for the floating-point root),
+ * s[k] = sum over the pairs of (x[i] y[j])^p is computed exactly -- v^p in
+ * limbs of b bits, the limb index on e extra axes, one HC_INT64 convolution
+ * of D + e axes (every entry below 2^63) -- and z[k] is the integer nearest
+ * s[k]^(1/p), which the bound makes the maximum.
+ *   hc_maxconv_plan: p, the limb width b, the limb axes e and the limb count
+ *     L for (D, vmax); HC_ERR_ARG when no plan exists: D or vmax out of range
+ *     (vmax in 0 .. 2^31 - 1, and at most 2^19 unless p = 1, since for p > 1
+ *     the root is taken in double precision), p above 2^24, more than 12
+ *     limb axes, or D + e > HC_MAX_D.  Any output pointer may be NULL.
+ *   hc_maxconv_workspace_size: bytes of workspace (0 when no plan exists):
+ *     the power table, the two limb cubes (2^(D+e) int64 each), the
+ *     3^(D+e) int64 convolution and that convolution's own workspace (the
+ *     default HC_INT64 schedule's, so a schedule installed with
+ *     hc_set_default_schedule changes it).
+ *   hc_maxconv: x, y (2^D int64, const), z (3^D int64, overwritten); the
+ *     plain form's alignment, aliasing and workspace rules.  The call clears
+ *     the workspace status word on `stream`; an entry outside [0, vmax] is
+ *     recorded there as HC_ERR_ARG (read it with hc_device_status), and z is
+ *     then unspecified.  Cost: 3^(D+e) outputs of the int64 convolution for
+ *     3^D results -- the price of exactness beyond 64 bits.
+ */
+hc_status hc_maxconv_plan(int D, int64_t vmax, int* p, int* limb_bits, int* limb_axes,
+                          int* limbs);
+
+size_t hc_maxconv_workspace_size(int D, int64_t vmax);
+
+hc_status hc_maxconv(const int64_t* x, const int64_t* y, int64_t* z, int D, int64_t vmax,
+                     void* workspace, size_t ws_bytes, hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * No-allocation form.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory at the call site -- code
  * running while another framework owns the device's memory pool,

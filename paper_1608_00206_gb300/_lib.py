@@ -63,6 +63,10 @@ SIGNATURES = {
     "hc_batched_prepare_split": (_i, [ctypes.POINTER(hc_instance), _i, _i, _i, _vp, _sz, _vp]),
     "hc_batched_autotune": (_i, [ctypes.POINTER(hc_instance), _i, _i, _vp, _sz, _i, _vp,
                                  ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)]),
+    "hc_maxconv_plan": (_i, [_i, ctypes.c_int64, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                             ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "hc_maxconv_workspace_size": (_sz, [_i, ctypes.c_int64]),
+    "hc_maxconv": (_i, [_vp, _vp, _vp, _i, ctypes.c_int64, _vp, _sz, _vp]),
     "hc_device_status": (_i, [_vp, _vp]),
     "hc_probe_alu_rate": (_i, [_i, ctypes.POINTER(ctypes.c_double), _vp]),
     "hc_profile_enable": (_i, [_i]),

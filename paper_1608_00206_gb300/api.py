@@ -428,3 +428,48 @@ def carry_free_convolve(x: torch.Tensor, y: torch.Tensor, *, mixed: bool = False
     check(lib.hc_carryfree(_ptr(x), _ptr(y), _ptr(z), N, code, _ptr(ws), nbytes,
                            _stream(x.device, stream)), "hc_carryfree")
     return z
+
+
+def maxconv_plan(D: int, vmax: int) -> dict:
+    """The library's plan for max-convolution of (D, vmax) (hc_maxconv_plan):
+    p, limb width b, limb axes e and limb count L.  Raises HCError when no
+    plan exists."""
+    p, b, e, L = (ctypes.c_int() for _ in range(4))
+    check(_lib.lib().hc_maxconv_plan(int(D), int(vmax), ctypes.byref(p), ctypes.byref(b),
+                                     ctypes.byref(e), ctypes.byref(L)), "hc_maxconv_plan")
+    return {"p": p.value, "b": b.value, "e": e.value, "L": L.value}
+
+
+def maxconv(x: torch.Tensor, y: torch.Tensor, vmax: int, out: torch.Tensor | None = None, *,
+            workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Max-convolution of int64 CUDA hypercubes with entries in [0, vmax]
+    (paper, Discussion; hc_maxconv): z[k] = max of x[i] * y[j] over the pairs
+    i + j = k, exact, through the p-norm ring (sums of p-th powers in limbs,
+    one int64 convolution of D + e axes, nearest integer p-th roots).  Entries
+    outside [0, vmax] are reported by :func:`device_status` on the workspace
+    (HC_ERR_ARG) when a workspace is passed in, and make z unspecified."""
+    if x.dtype != torch.int64 or y.dtype != torch.int64:
+        raise TypeError("max-convolution takes int64 tensors")
+    if not (x.is_cuda and y.is_cuda and x.device == y.device):
+        raise ValueError("max-convolution takes CUDA tensors on one device")
+    if x.numel() != y.numel():
+        raise ValueError("x and y differ in length")
+    D = dim_of(x)
+    x, y = x.contiguous(), y.contiguous()
+    if out is None:
+        out = torch.empty(_out_shape(x, D), dtype=torch.int64, device=x.device)
+    lib = _lib.lib()
+    tuning.ensure_installed(x.device)
+    nbytes = int(lib.hc_maxconv_workspace_size(D, int(vmax)))
+    if nbytes == 0:
+        raise _lib.HCError(_lib.HC_ERR_ARG, f"hc_maxconv: no plan for D={D}, vmax={vmax}")
+    ws = _workspace(nbytes, x.device, workspace)
+    check(lib.hc_maxconv(_ptr(x), _ptr(y), _ptr(out), D, int(vmax), _ptr(ws), nbytes,
+                         _stream(x.device, stream)), "hc_maxconv")
+    return out
+
+
+def device_status(workspace: torch.Tensor, stream=None) -> int:
+    """The status word a kernel recorded in `workspace` (hc_device_status;
+    synchronises the stream)."""
+    return int(_lib.lib().hc_device_status(_ptr(workspace), _stream(workspace.device, stream)))

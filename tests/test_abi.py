@@ -227,3 +227,52 @@ def test_lowmem_workspace_is_small(L):
     bad = _lib.hc_schedule(_lib.HC_SCHED_LOWMEM, 8, 6, 16, 32, 6)
     assert L.hc_convolve_schedule(x, y, z, 6, _lib.HC_INT64, ctypes.byref(bad), ws, 1 << 20,
                                   None) == _lib.HC_ERR_ARG
+
+
+def test_maxconv_plan_matches_the_oracle(L, oracle):
+    """hc_maxconv_plan's p is the oracle's exact choice (the smallest p with
+    M (2^(D/p) - 1) < 7/16, decided in integers), and its limbs hold vmax^p
+    with every convolution entry below 2^63."""
+    for D in range(0, 17):
+        for vmax in (0, 1, 2, 3, 5, 7, 15, 40):
+            p, b, e, n = (ctypes.c_int() for _ in range(4))
+            st = L.hc_maxconv_plan(D, vmax, ctypes.byref(p), ctypes.byref(b), ctypes.byref(e),
+                                   ctypes.byref(n))
+            if st != _lib.HC_OK:
+                assert st == _lib.HC_ERR_ARG
+                assert L.hc_maxconv_workspace_size(D, vmax) == 0
+                # refused only where the oracle's own plan needs more than 12
+                # limb axes or more than HC_MAX_D axes in all
+                try:
+                    _, _, eo, _ = oracle.maxconv_limb_plan(D, vmax)
+                    assert eo > 12 or D + eo > _lib.HC_MAX_D
+                except ValueError:
+                    pass
+                continue
+            assert p.value == oracle.maxconv_p(D, vmax), (D, vmax)
+            bits = max(1, (vmax ** p.value).bit_length()) if vmax > 1 else 1
+            assert n.value * b.value >= bits and n.value <= (1 << e.value)
+            assert D + e.value + 2 * b.value <= 63 and 1 <= b.value <= 31
+            De = D + e.value
+            nb = L.hc_maxconv_workspace_size(D, vmax)
+            assert nb >= 2 * (8 << De) + 8 * 3 ** De + L.hc_workspace_size(De, _lib.HC_INT64)
+
+
+def test_maxconv_arguments_caught_on_host(L):
+    """hc_maxconv rejects bad arguments before any CUDA call."""
+    D, vmax = 6, 3
+    nb = L.hc_maxconv_workspace_size(D, vmax)
+    assert nb > 0
+    x, y, z, ws = FAKE, FAKE + (1 << 20), FAKE + (1 << 24), FAKE + (1 << 30)
+    mc = L.hc_maxconv
+    assert mc(x, y, z, -1, vmax, ws, nb, None) == _lib.HC_ERR_ARG
+    assert mc(x, y, z, D, -1, ws, nb, None) == _lib.HC_ERR_ARG
+    assert mc(x, y, z, D, 1 << 40, ws, nb, None) == _lib.HC_ERR_ARG
+    assert mc(x, y, z, 20, 1000, ws, nb, None) == _lib.HC_ERR_ARG   # no plan
+    assert mc(None, y, z, D, vmax, ws, nb, None) == _lib.HC_ERR_ARG
+    assert mc(x, y, z, D, vmax, None, nb, None) == _lib.HC_ERR_ARG
+    assert mc(x + 8, y, z, D, vmax, ws, nb, None) == _lib.HC_ERR_ALIGN
+    assert mc(x, y, z, D, vmax, ws + 16, nb, None) == _lib.HC_ERR_ALIGN
+    assert mc(x, y, z, D, vmax, ws, nb - 1, None) == _lib.HC_ERR_WORKSPACE
+    assert mc(x, y, x + 16, D, vmax, ws, nb, None) == _lib.HC_ERR_ALIAS
+    assert mc(x, y, z, D, vmax, z, nb, None) == _lib.HC_ERR_ALIAS
