@@ -57,9 +57,13 @@ WORKLOADS = {
                "replayed from one CUDA graph",
     "fwdbwd": "D=18 float32, x,y,w iid N(0,1), loss = sum(w*z), forward + hand-written adjoint "
               "via torch.autograd",
+    "maxconv": "D=14 max-convolution of bounded non-negative integers: x,y 2^14 iid uniform "
+               "integers in [0,3]; p-norm ring (sums of p-th powers in limbs on 4 extra "
+               "carry-free axes, one 18-axis int64 convolution, nearest-integer roots); z 3^14 "
+               "int64",
 }
 DEFAULT_STEPS = {"d20_int64": 30, "d16_fp64": 30, "d16_mixed": 50, "d16_ff": 50, "d10_int64": 200,
-                 "d18_fp32": 50, "batched": 20, "fwdbwd": 30}
+                 "d18_fp32": 50, "batched": 20, "fwdbwd": 30, "maxconv": 30}
 SINGLE = ("d20_int64", "d16_fp64", "d16_mixed", "d16_ff", "d10_int64", "d18_fp32")
 
 
@@ -242,6 +246,24 @@ class Workload:
             self.alg_bytes = sum(4 * (3 ** d + 2 * 2 ** d) for d in self.dims)
             self.dtype = "f32"
             self.D = None
+        elif name == "maxconv":
+            D = D_override or 14
+            vmax = 3
+            x, y = inputs.uniform_int_pair(D, 0, vmax, seed)
+            self.D = D
+            self.vmax = vmax
+            self.plan = hc.maxconv_plan(D, vmax)
+            self.conv_D = D + self.plan["e"]
+            self.host = (x, y)
+            self.x = torch.from_numpy(x).to(dev)
+            self.y = torch.from_numpy(y).to(dev)
+            self.z = torch.empty(3 ** D, dtype=torch.int64, device=dev)
+            nb = hc.maxconv_workspace_size(D, vmax)
+            self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            self.outputs = 3 ** D
+            # the result needs x, y read and z written once
+            self.alg_bytes = 8 * (3 ** D + 2 * 2 ** D)
+            self.dtype = "int64"
         elif name == "fwdbwd":
             D = D_override or 18
             self.D = D
@@ -293,6 +315,8 @@ class Workload:
             self.batch.replay()
         elif self.graph is not None:
             self.graph.replay()
+        elif self.name == "maxconv":
+            self.hc.maxconv(self.x, self.y, self.vmax, out=self.z, workspace=self.ws)
         elif self.name == "fwdbwd":
             self.x.grad = None
             self.y.grad = None
@@ -308,42 +332,50 @@ class Workload:
 
         from paper_1608_00206_gb300 import _lib
         code = {"d20_int64": 0, "d10_int64": 0, "d16_fp64": 1, "d18_fp32": 2,
-                "d16_mixed": 3, "d16_ff": 4}[self.name]
+                "d16_mixed": 3, "d16_ff": 4, "maxconv": 0}[self.name]
+        # the max-convolution's own convolution has D + e axes
+        Dc = getattr(self, "conv_D", self.D)
         cmax = 9 if code == 2 else 8
         if self.sched.get("lowmem"):
             # leaves of D - top axes on the whole-array-pass plan
-            C = min(self.sched.get("c") or 8, self.D - self.sched["top"])
-            return 1, C, 0, self.D - C, self.D - C
+            C = min(self.sched.get("c") or 8, Dc - self.sched["top"])
+            return 1, C, 0, Dc - C, Dc - C
         if self.sched.get("top"):
-            C = min(self.sched.get("c") or 8, self.D - self.sched["top"])
-            return 4, C, self.sched["top"], self.D - self.sched["top"] - C, 0
+            C = min(self.sched.get("c") or 8, Dc - self.sched["top"])
+            return 4, C, self.sched["top"], Dc - self.sched["top"] - C, 0
         if self.sched:
             kind = (3 if self.sched.get("bulk") else 2) if "m" in self.sched else 1
             c, k = self.sched.get("c", 0), self.sched.get("m", self.sched.get("kmax", 0))
         else:
             s = _lib.hc_schedule()
-            _lib.lib().hc_get_default_schedule(self.D, code, ctypes.byref(s))
+            _lib.lib().hc_get_default_schedule(Dc, code, ctypes.byref(s))
             kind, c, k = s.kind, s.c, s.k
             if kind == 6:
                 kind = 1  # padded whole-array passes: the same geometry
             if kind in (4, 5):  # hybrid / low-workspace defaults (int64)
-                C = min(c or 8, self.D - s.top)
+                C = min(c or 8, Dc - s.top)
                 if kind == 5:
-                    return 1, C, 0, self.D - C, self.D - C
-                return 4, C, s.top, self.D - s.top - C, 0
-        C = min(c or cmax, self.D)
+                    return 1, C, 0, Dc - C, Dc - C
+                return 4, C, s.top, Dc - s.top - C, 0
+        C = min(c or cmax, Dc)
         if kind == 1:
-            return kind, C, 0, self.D - C, self.D - C
-        m = min(self.D - C, k or 6)
-        ap = self.D - C - m
+            return kind, C, 0, Dc - C, Dc - C
+        m = min(Dc - C, k or 6)
+        ap = Dc - C - m
         return kind, C, m, ap, ap + (m if kind == 3 else max(m - 3, 0))
 
     # per-kernel algorithmic bytes (or FP64 operations) per launch
     def kernel_alg(self, kname, launches_per_step):
-        D = self.D
+        D = getattr(self, "conv_D", self.D)
         if self.name == "batched":
             return self._batched_bytes(kname) / max(launches_per_step, 1), "hbm"
-        s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64", "d16_ff") else 4
+        if kname == "maxconv_root":
+            # read the 3^(D+e) convolution once, write the 3^D maxima
+            return 8 * (3 ** D + 3 ** self.D), "hbm"
+        if kname == "maxconv_spread":
+            # read x, y; write the two limb cubes of 2^(D+e) each
+            return 8 * (2 * 2 ** self.D + 2 * 2 ** D), "hbm"
+        s = 8 if self.name in ("d20_int64", "d10_int64", "d16_fp64", "d16_ff", "maxconv") else 4
         sw = 8 if self.name in ("d16_mixed", "d16_ff") else s
         if kname in ("chunk", "slab"):
             kind, C, m, ap, ev = self.schedule_geometry()
@@ -545,6 +577,16 @@ def _comparisons(wl, ms_per_step):
         t = timed(lambda: hc.convolve(wl.x, wl.y, out=z, workspace=ws, top=4, c=8, kmax=6,
                                       cols=32), reps=10)
         return {"hybrid_top4_ms": t, "hybrid_over_default": t / ms_per_step}
+    if wl.name == "maxconv":
+        # the (sum) convolution of the same inputs, and of the D + e axes the
+        # p-norm ring convolves
+        z = torch.empty(3 ** wl.D, dtype=torch.int64, device=wl.dev)
+        nb = hc.workspace_size(wl.D, torch.int64)
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=wl.dev)
+        t = timed(lambda: hc.convolve(wl.x, wl.y, out=z, workspace=ws), reps=10)
+        return {"plain_int64_ms": t, "maxconv_over_plain_int64": ms_per_step / t,
+                "p": wl.plan["p"], "limb_bits": wl.plan["b"], "limb_axes": wl.plan["e"],
+                "limbs": wl.plan["L"], "convolution_axes": wl.conv_D}
     if wl.name in ("d16_mixed", "d16_ff"):
         z = torch.empty(3 ** wl.D, dtype=torch.float32, device=wl.dev)
         nb = hc.workspace_size(wl.D, torch.float32)
@@ -586,7 +628,7 @@ def _e2e(wl, steps=3, warmup=1):
     import torch
 
     hc = wl.hc
-    if wl.name in ("batched", "fwdbwd"):
+    if wl.name in ("batched", "fwdbwd", "maxconv"):
         return _e2e_other(wl, steps, warmup)
     x, y = wl.host
     xh = torch.from_numpy(x).pin_memory()
@@ -632,6 +674,19 @@ def _e2e_other(wl, steps, warmup):
 
         def one():
             b.run_host(xh, yh, zh)
+    elif wl.name == "maxconv":
+        x, y = wl.host
+        xh, yh = (torch.from_numpy(a).pin_memory() for a in (x, y))
+        zh = torch.empty(3 ** wl.D, dtype=torch.int64, pin_memory=True)
+        h2d = x.nbytes + y.nbytes
+        d2h = zh.numel() * 8
+
+        def one():
+            xd = xh.to(wl.dev, non_blocking=True)
+            yd = yh.to(wl.dev, non_blocking=True)
+            hc.maxconv(xd, yd, wl.vmax, out=wl.z, workspace=wl.ws)
+            zh.copy_(wl.z, non_blocking=True)
+            torch.cuda.synchronize(wl.dev)
     else:
         x, y, w = wl.host
         xh, yh, wh = (torch.from_numpy(a).pin_memory() for a in (x, y, w))
@@ -712,6 +767,10 @@ def _oracle_samples(name):
             oracle.adjoint(w, x, y)
             return z.size
         return "the full D=18 forward (all cores) and adjoint (single thread)", [f], thr
+    if name == "maxconv":
+        x, y = inputs.uniform_int_pair(14, 0, 3, seed)
+        return ("the full D=14 max-convolution from its definition (the oracle's pair loop, "
+                "single thread)", [lambda: oracle.maxconv_brute(x, y).size], 1)
     raise ValueError(name)
 
 
@@ -754,7 +813,8 @@ def _reference_arm(args, rank, world):
 
 def _dtype_name(w):
     return {"d20_int64": "int64", "d10_int64": "int64", "d16_fp64": "f64", "d16_mixed": "f32+ff",
-            "d16_ff": "ff", "d18_fp32": "f32", "batched": "f32", "fwdbwd": "f32"}[w]
+            "d16_ff": "ff", "d18_fp32": "f32", "batched": "f32", "fwdbwd": "f32",
+            "maxconv": "int64"}[w]
 
 
 # ------------------------------------------------------------------- main
@@ -814,7 +874,7 @@ SWEEP_STEPS = {14: 200, 15: 100, 16: 60, 17: 40, 18: 30, 19: 20}
 # The training-system forms beside the plain method, each timed after the
 # headline: (workload, steps).
 FORMS = (("batched", 20), ("fwdbwd", 30), ("d16_fp64", 30), ("d16_mixed", 50),
-         ("d16_ff", 50), ("d18_fp32", 50))
+         ("d16_ff", 50), ("d18_fp32", 50), ("maxconv", 30))
 
 
 def _brief(res):

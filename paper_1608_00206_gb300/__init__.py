@@ -11,14 +11,14 @@ from . import inputs  # noqa: F401  (numpy-only input generators)
 
 __all__ = ["inputs", "convolve", "convolve_backward", "convolve_batched", "BatchedConv",
            "hypercube_conv", "HypercubeConv", "workspace_size", "carry_free_convolve", "packed_offsets",
-           "maxconv", "maxconv_plan", "device_status", "build"]
+           "maxconv", "maxconv_plan", "maxconv_workspace_size", "device_status", "build"]
 
 
 def __getattr__(name):
     if name in ("convolve", "convolve_backward", "convolve_batched", "BatchedConv",
                 "hypercube_conv", "HypercubeConv", "workspace_size", "backward_workspace_size",
                 "dim_of", "HCError", "carry_free_convolve", "packed_offsets", "maxconv",
-                "maxconv_plan", "device_status"):
+                "maxconv_plan", "maxconv_workspace_size", "device_status"):
         from . import api
         return getattr(api, name)
     if name == "build":

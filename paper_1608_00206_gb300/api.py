@@ -440,6 +440,14 @@ def maxconv_plan(D: int, vmax: int) -> dict:
     return {"p": p.value, "b": b.value, "e": e.value, "L": L.value}
 
 
+def maxconv_workspace_size(D: int, vmax: int) -> int:
+    """Bytes of workspace hc_maxconv needs for (D, vmax) with the default
+    (tuned, once installed) int64 schedule; 0 when no plan exists."""
+    if torch.cuda.is_available():
+        tuning.ensure_installed(torch.device("cuda", torch.cuda.current_device()))
+    return int(_lib.lib().hc_maxconv_workspace_size(int(D), int(vmax)))
+
+
 def maxconv(x: torch.Tensor, y: torch.Tensor, vmax: int, out: torch.Tensor | None = None, *,
             workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Max-convolution of int64 CUDA hypercubes with entries in [0, vmax]

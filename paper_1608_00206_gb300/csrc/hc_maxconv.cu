@@ -174,58 +174,84 @@ __global__ void __launch_bounds__(256) maxconv_spread_kernel(
 // of W[d * n3 + k] 2^(value(d) b), value(d) = sum_j digit_j(d) 2^j (digit j
 // the j-th least significant base-3 digit).
 // p = 1 (D = 0, or vmax = 0): s is the single product itself, summed exactly
-// in 64-bit integers.  p > 1: s is accumulated as acc 2^(top b) in double;
-// every term is non-negative, so the only errors are the roundings of the
-// conversions and additions (relative < 3^e 2^-52, and a term 2^1000 below
-// the running sum underflowing to zero changes nothing at that precision),
-// then lg = top b + log2(acc) and q = 2^(lg / p).  Since lg / p is about
-// log2 of the result (<= 38), q carries a relative error of a few 1e-14 (plus
-// 3^e 2^-52 / p, which the plans keep smaller): below 0.01 for results up to
-// vmax^2 <= 2^38, well inside the 1/16 margin the choice of p leaves.
+// in 64-bit integers.  p > 1: s is accumulated in integers as
+// A 2^(top b - G), A unsigned 128-bit, top the largest value(d) with a
+// non-zero entry so far: a new top shifts A down, a lower term is shifted
+// down into A, dropping bits below A's unit.  With G = 62 - ceil(e log2 3)
+// the at most 3^e terms below 2^(63 + G) each keep A below 2^126, and the
+// dropped bits (below 1 per term against A >= 2^G) leave s with a relative
+// error below 3^e 2^-G <= 2^-23.  The root divides that by p, and the choice
+// of p makes M / p <= 7 / (16 D ln 2): the root is off by less than
+// 2^-23 0.63 / D.  Then q = 2^(lg / p), lg = log2(A) + top b - G in double
+// precision once per output (relative error a few 1e-14, i.e. below 0.01
+// for results up to vmax^2 <= 2^38), and the nearest integer: both well
+// inside the 1/16 margin the choice of p leaves.
 __global__ void __launch_bounds__(256) maxconv_root_kernel(const long long* __restrict__ W,
                                                            long long* __restrict__ z,
-                                                           long long n3, int e, int b, int p) {
-  long long n_d = 1;
-  for (int j = 0; j < e; ++j) n_d *= 3;
+                                                           long long n3, int e, int b, int p,
+                                                           int G) {
+  typedef unsigned __int128 u128;
+  // digit strings in groups of 3^eg (the eg lowest digits), loaded together
+  const int eg = e < 2 ? e : 2;
+  const int gsz = eg == 0 ? 1 : (eg == 1 ? 3 : 9);
+  const int eh = e - eg;  // digits counted by the group counter
+  long long n_g = 1;
+  for (int j = 0; j < eh; ++j) n_g *= 3;
+  // value of the eg lowest digits of the r-th member of a group
+  const int off9[9] = {0, 1, 2, 2, 3, 4, 4, 5, 6};
   const double inv_p = 1.0 / (double)p;
 #pragma unroll 1
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n3;
        k += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    u128 A = 0;
     unsigned long long exact = 0;  // p = 1: s in Z/2^64
     int top = -1;
-    int val = 0;          // value(d), kept alongside the base-3 counter
-    unsigned int dig = 0; // base-3 digits of d, two bits each (e <= 12)
-    for (long long d = 0; d < n_d; ++d) {
-      const long long w = __ldcs(W + d * n3 + k);
-      if (w != 0) {
+    int vbase = 0;         // value of the group's upper digits
+    unsigned int dig = 0;  // base-3 digits eg.. of d, two bits each (e <= 12)
+#pragma unroll 1
+    for (long long g = 0; g < n_g; ++g) {
+      long long w[9];
+      const long long* src = W + (g * gsz) * n3 + k;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) w[r] = r < gsz ? __ldcs(src + r * n3) : 0;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        if (r >= gsz || w[r] == 0) continue;
+        const int val = vbase + (eg == 1 ? r : off9[r]);
+        const unsigned long long t = (unsigned long long)w[r];
         if (p == 1) {
-          exact += (unsigned long long)w << (val * b);
+          exact += t << (val * b);
+        } else if (top < 0) {
+          top = val;
+          A = (u128)t << G;
+        } else if (val > top) {
+          const int sh = (val - top) * b;
+          A = sh >= 128 ? (u128)0 : (A >> sh);
+          top = val;
+          A += (u128)t << G;
         } else {
-          const double t = (double)w;
-          if (val > top) {
-            acc = (top < 0) ? t : ldexp(acc, (top - val) * b) + t;
-            top = val;
-          } else {
-            acc += ldexp(t, (val - top) * b);
-          }
+          const int sh = (top - val) * b - G;
+          if (sh <= 0) A += (u128)t << (-sh);
+          else if (sh < 64) A += (u128)(t >> sh);
         }
       }
-      // d + 1: base-3 increment, value(d) follows the digits
-      for (int j = 0; j < e; ++j) {
+      // next group: base-3 increment of the upper digits, value alongside
+      for (int j = 0; j < eh; ++j) {
         const unsigned int q = (dig >> (2 * j)) & 3u;
         if (q < 2) {
           dig += 1u << (2 * j);
-          val += 1 << j;
+          vbase += 1 << (j + eg);
           break;
         }
         dig &= ~(3u << (2 * j));
-        val -= 2 << j;
+        vbase -= 2 << (j + eg);
       }
     }
     long long out = (long long)exact;
     if (p > 1 && top >= 0) {
-      const double lg = (double)top * (double)b + log2(acc);
+      const double a = (double)(unsigned long long)(A >> 64) * 18446744073709551616.0 +
+                       (double)(unsigned long long)A;
+      const double lg = log2(a) + (double)top * (double)b - (double)G;
       out = llrint(exp2(lg * inv_p));
     }
     z[k] = out;
@@ -303,7 +329,10 @@ extern "C" hc_status hc_maxconv(const int64_t* x, const int64_t* y, int64_t* z, 
     const long long n3 = (long long)pow3z(D);
     long long blocks = (n3 + 255) / 256;
     if (blocks > cap) blocks = cap;
-    maxconv_root_kernel<<<(unsigned)blocks, 256, 0, st>>>(W, (long long*)z, n3, P.e, P.b, P.p);
+    int lg3e = 0;  // ceil(e log2 3)
+    while ((double)lg3e < P.e * 1.5849625007211562) ++lg3e;
+    maxconv_root_kernel<<<(unsigned)blocks, 256, 0, st>>>(W, (long long*)z, n3, P.e, P.b, P.p,
+                                                          62 - lg3e);
     s = record_cuda_error(cudaGetLastError());
   }
   return s;

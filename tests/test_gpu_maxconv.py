@@ -85,7 +85,7 @@ def test_maxconv_out_of_range_entry_is_reported(hc):
     status word; the next call with valid entries clears it."""
     D, vmax = 5, 3
     x, y = inputs.uniform_int_pair(D, 0, vmax, seed=6)
-    nb = int(_lib.lib().hc_maxconv_workspace_size(D, vmax))
+    nb = hc.maxconv_workspace_size(D, vmax)
     ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
     bad = x.copy()
     bad[3] = vmax + 1
