@@ -55,8 +55,8 @@ WORKLOADS = {
     "batched": "4096 float32 instances, D iid uniform in 6..14, x,y iid U[0,1); fused "
                "persistent launch and per-D grouped passes at the autotuned fusion depth, "
                "replayed from one CUDA graph",
-    "fwdbwd": "D=18 float32, x,y,w iid N(0,1), loss = sum(w*z), forward + hand-written adjoint "
-              "via torch.autograd",
+    "fwdbwd": "D=18 float32, x,y,w iid N(0,1), loss = sum(w*z) (torch.dot), forward + "
+              "hand-written adjoint via torch.autograd",
     "maxconv": "D=14 max-convolution of bounded non-negative integers: x,y 2^14 iid uniform "
                "integers in [0,3]; p-norm ring (sums of p-th powers in limbs on 4 extra "
                "carry-free axes, one 18-axis int64 convolution, nearest-integer roots); z 3^14 "
@@ -320,7 +320,8 @@ class Workload:
         elif self.name == "fwdbwd":
             self.x.grad = None
             self.y.grad = None
-            loss = (self.w * self.hc.hypercube_conv(self.x, self.y)).sum()
+            # sum(w * z) as one fused reduction (no 3^D temporary)
+            loss = self.torch.dot(self.w, self.hc.hypercube_conv(self.x, self.y))
             loss.backward()
         else:
             self.hc.convolve(self.x, self.y, out=self.z, mixed=self.mixed, workspace=self.ws,
@@ -699,7 +700,7 @@ def _e2e_other(wl, steps, warmup):
             xd = xh.to(wl.dev, non_blocking=True).requires_grad_()
             yd = yh.to(wl.dev, non_blocking=True).requires_grad_()
             wd = wh.to(wl.dev, non_blocking=True)
-            loss = (wd * hc.hypercube_conv(xd, yd)).sum()
+            loss = torch.dot(wd, hc.hypercube_conv(xd, yd))
             loss.backward()
             gxh.copy_(xd.grad, non_blocking=True)
             gyh.copy_(yd.grad, non_blocking=True)
