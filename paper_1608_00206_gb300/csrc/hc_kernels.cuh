@@ -118,7 +118,7 @@ struct InterpPipe {
   static constexpr bool kOn = K1 > 0 && 2 * kBuf <= 113 * 1024;
   static constexpr int kThreads = (p3(K2) * L + 31) / 32 * 32;
   static constexpr int kRegs = 2 * p3(K2) * (int)(sizeof(typename M::W) / 4) + 24;
-  static constexpr bool kReg = K1 > 0 && !kOn && kThreads * kRegs <= 65536;
+  static constexpr bool kReg = K1 > 0 && K1 <= K2 && !kOn && kThreads * kRegs <= 65536;
   static constexpr size_t kSmem = K1 == 0 ? 0 : (kOn ? 2 * kBuf : kBuf);
 };
 
@@ -364,6 +364,11 @@ inline cudaError_t launch_interp(int k, int cols, const typename M::W* src, void
     case 1: return launch_interp_k<M, 0, 1, FINAL, TR>(cols, src, dst, hi, lo, st);
     case 2: return launch_interp_k<M, 0, 2, FINAL, TR>(cols, src, dst, hi, lo, st);
     case 3: return launch_interp_k<M, 0, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
+    // K2 = 3: round 1 over 27-element pencils of the inner axes.  The
+    // balanced splits (2, 2) and (3, 2) -- fewer threads, every thread busy
+    // in both rounds -- measured slower here on GB300 (D = 18 float32 passes
+    // 1.57 -> 1.61 ms, D = 18 int64 2.38 -> 2.50 ms, adjoint I^T 1.50 ->
+    // 1.65 ms) and faster for the batched group passes, which use them.
     case 4: return launch_interp_k<M, 1, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
     case 5: return launch_interp_k<M, 2, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
     case 6: return launch_interp_k<M, 3, 3, FINAL, TR>(cols, src, dst, hi, lo, st);
