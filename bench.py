@@ -103,6 +103,30 @@ def _fp64_peak():
         return FP64_OPS_NOMINAL, "nominal GB300 FP64 rate (1.25 TFLOP/s with FMA = 2)"
     return m, ("measured FP64 add/multiply rate of this device (hc_probe_alu_rate: "
                "independent __dadd_rn/__dmul_rn chains, CUDA events)")
+_FP32_MEASURED = []
+FP32_OPS_NOMINAL = 2070e6 * 152 * 128  # 128 binary32 add/multiply lanes per SM at 2070 MHz
+
+
+def _fp32_peak():
+    """(ops/s, source): binary32 add/multiply rate measured by the library's
+    probe kernel, once per process (the roof of the float-float kernels)."""
+    if not _FP32_MEASURED:
+        import ctypes
+
+        import torch
+
+        from paper_1608_00206_gb300 import _lib
+        v = ctypes.c_double()
+        rc = _lib.lib().hc_probe_alu_rate(_lib.HC_FP32, ctypes.byref(v),
+                                          torch.cuda.current_stream().cuda_stream)
+        _FP32_MEASURED.append(float(v.value) if rc == 0 and v.value > 0 else None)
+    m = _FP32_MEASURED[0]
+    if m is None:
+        return FP32_OPS_NOMINAL, "nominal GB300 binary32 add/multiply rate"
+    return m, ("measured binary32 add/multiply rate of this device (hc_probe_alu_rate: "
+               "independent __fadd_rn/__fmul_rn chains, CUDA events)")
+
+
 L2_BYTES = 129 << 20  # GB300 L2 (rounded up)
 L2_FLUSH_BYTES = 256 << 20
 
@@ -380,6 +404,17 @@ class Workload:
         sw = 8 if self.name in ("d16_mixed", "d16_ff") else s
         if kname in ("chunk", "slab"):
             kind, C, m, ap, ev = self.schedule_geometry()
+            if self.name in ("d16_mixed", "d16_ff") and kname == "slab":
+                # binary32 operations: per tile the evaluation of both
+                # operands on C axes (3^C - 2^C additions each: 1 operation
+                # binary32, 11 float-float), 3^C products (1, or 9 for the
+                # float-float product), per unit the interpolation of its
+                # C + m axes (a third of the elements per axis are middles,
+                # each two float-float subtractions of 11 operations)
+                ea, mu = (1, 1) if self.name == "d16_mixed" else (11, 9)
+                tile = 2 * (3 ** C - 2 ** C) * ea + 3 ** C * mu
+                interp = (C + m) * 3 ** (C + m - 1) * 22
+                return 3 ** ap * (3 ** m * tile + interp), "alu32"
             if self.name == "d16_fp64":
                 tile = 2 * (3 ** C - 2 ** C) + 3 ** C + 2 * C * 3 ** (C - 1)
                 return 3 ** ap * (3 ** m * tile + 2 * m * 3 ** (C + m - 1)), "alu"
@@ -835,6 +870,14 @@ def _roofline(wl, prof, steps):
     if alg is None:
         return {"bound": "hbm", "kernel": kname, "achieved": None, "peak": peak_hbm,
                 "unit": "GB/s", "frac": None, "traffic": None}
+    if bound == "alu32":
+        achieved = alg / (per_launch_ms / 1e3) / 1e12
+        peak, source = _fp32_peak()
+        return {"bound": "alu", "kernel": kname, "achieved": achieved,
+                "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (peak / 1e12), "traffic": None,
+                "ms_per_launch": per_launch_ms, "peak_source": source,
+                "frac_of_nominal": achieved / (FP32_OPS_NOMINAL / 1e12)}
     if bound == "alu":
         achieved = alg / (per_launch_ms / 1e3) / 1e12
         peak, source = _fp64_peak()

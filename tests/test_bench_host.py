@@ -95,3 +95,30 @@ def test_brief_keeps_the_reported_fields():
     assert b["dominant"]["kernel"] == "interp_pass" and b["dominant"]["frac"] == 0.7512
     assert "peak_source" not in b["dominant"]
     assert b["kernels"] == res["kernels"] and b["clocks"] == res["clocks"]
+
+
+def test_roofline_float_float_slab_takes_the_measured_fp32_rate(monkeypatch):
+    """The float-float chunk kernels are arithmetic-bound: their roofline is
+    binary32 operations per launch against the probe's binary32 rate."""
+    monkeypatch.setattr(bench, "_fp32_peak", lambda: (30e12, "measured probe"))
+    wl = _FakeWorkload("d16_mixed", 16, alg=5e9, bound="alu32")
+    r = bench._roofline(wl, {"slab": (4, 2.0), "interp_pass": (4, 1.0)}, steps=4)
+    assert r["kernel"] == "slab" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == pytest.approx(30.0)
+    assert r["achieved"] == pytest.approx(5e9 / 0.5e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 30.0)
+
+
+def test_float_float_slab_operation_count():
+    """The counted operations of the chunked-bulk kernel for the float-float
+    forms: tile evaluation, products and interpolation of the unit's axes
+    (D = 16, C = 8, m = 6 middle axes, 3^2 units)."""
+    wl = bench.Workload.__new__(bench.Workload)
+    wl.D, wl.sched = 16, {}
+    wl.schedule_geometry = lambda: (3, 8, 6, 2, 8)
+    for name, ea, mu in (("d16_mixed", 1, 1), ("d16_ff", 11, 9)):
+        wl.name = name
+        ops, bound = bench.Workload.kernel_alg(wl, "slab", 1)
+        tile = 2 * (3 ** 8 - 2 ** 8) * ea + 3 ** 8 * mu
+        assert bound == "alu32"
+        assert ops == 9 * (3 ** 6 * tile + 14 * 3 ** 13 * 22)
