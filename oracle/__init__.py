@@ -25,8 +25,9 @@ and marshals numpy arrays.  Functions and the passages they follow:
   respect to x and y (transpose of the recurrence; brute-force correlation).
 * :func:`zabs` -- magnitude companion for the forward-error bound
   ``|z_hat - z| <= gamma_{3D+1} * zabs``.
-* :func:`maxconv_brute` -- max-convolution (Discussion, the (x, max)
-  semiring) from its definition, in C++.
+* :func:`maxconv_brute`, :func:`maxconv_points` -- max-convolution
+  (Discussion, the (x, max) semiring) from its definition, in C++: every
+  output, or chosen outputs one at a time.
 * :func:`maxconv_p`, :func:`maxconv_pnorm`, :func:`maxconv_limb_plan`,
   :func:`maxconv_limb_sums` -- the Discussion's p-norm route to exact
   max-convolution of bounded non-negative integers, in Python integers
@@ -87,6 +88,7 @@ def _lib():
             lib.oracle_adjoint_brute.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_zabs.argtypes = [vp, vp, vp, i]
             lib.oracle_maxconv_brute.argtypes = [vp, vp, vp, i]
+            lib.oracle_maxconv_points.argtypes = [vp, vp, i, vp, sz, vp]
             lib.oracle_max_threads.restype = i
             _LIB = lib
     return _LIB
@@ -290,6 +292,21 @@ def maxconv_brute(x, y) -> np.ndarray:
     if _lib().oracle_maxconv_brute(_ptr(x), _ptr(y), _ptr(z), D):
         raise RuntimeError("oracle_maxconv_brute failed")
     return z
+
+
+def maxconv_points(x, y, ks) -> np.ndarray:
+    """Max-convolution at chosen flat output indices k, each from its
+    2^{#ones(k)} pairs (the definition, one output at a time)."""
+    x = np.ascontiguousarray(x, dtype=np.int64).reshape(-1)
+    y = np.ascontiguousarray(y, dtype=np.int64).reshape(-1)
+    D = dim_of(x)
+    ks = np.ascontiguousarray(ks, dtype=np.uint64).reshape(-1)
+    if ks.size and int(ks.max()) >= 3 ** D:
+        raise ValueError("output index out of range")
+    out = np.empty(ks.size, dtype=np.int64)
+    if _lib().oracle_maxconv_points(_ptr(x), _ptr(y), D, _ptr(ks), ks.size, _ptr(out)):
+        raise RuntimeError("oracle_maxconv_points failed")
+    return out
 
 
 def maxconv_bound_holds(D: int, vmax: int, p: int, num: int = 7, den: int = 16) -> bool:

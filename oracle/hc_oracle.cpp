@@ -126,6 +126,33 @@ void maxconv_brute(const int64_t* x, const int64_t* y, int64_t* z, int D) {
     }
 }
 
+// One output of the max-convolution: the largest x[i]*y[j] over the
+// 2^{#ones(k)} pairs with i+j = k (digit 0 forces (0,0), 2 forces (1,1), 1
+// allows (0,1) and (1,0)), straight from the definition.
+int64_t maxconv_point(const int64_t* x, const int64_t* y, int D, size_t k) {
+  int dig[64];
+  size_t kk = k;
+  for (int d = D - 1; d >= 0; --d) { dig[d] = (int)(kk % 3); kk /= 3; }
+  int ones[64], m = 0;
+  size_t ibase = 0;
+  for (int d = 0; d < D; ++d) {
+    const size_t bit = (size_t)1 << (D - 1 - d);
+    if (dig[d] == 2) ibase |= bit;
+    if (dig[d] == 1) ones[m++] = d;
+  }
+  int64_t best = INT64_MIN;
+  for (size_t s = 0; s < ((size_t)1 << m); ++s) {
+    size_t i = ibase, j = ibase;
+    for (int q = 0; q < m; ++q) {
+      const size_t bit = (size_t)1 << (D - 1 - ones[q]);
+      if ((s >> (m - 1 - q)) & 1u) i |= bit; else j |= bit;
+    }
+    const int64_t v = x[i] * y[j];
+    if (v > best) best = v;
+  }
+  return best;
+}
+
 // ---------------------------------------------------------------------------
 // The Methods recurrence (3-way split), on fresh temporaries:
 //   z[0] = x[0]*y[0];  z[2] = x[1]*y[1];
@@ -648,6 +675,13 @@ int oracle_zabs(const double* absx, const double* absy, double* z, int D) {
 int oracle_maxconv_brute(const int64_t* x, const int64_t* y, int64_t* z, int D) {
   if (D < 0 || D > 20) return 1;
   maxconv_brute(x, y, z, D);
+  return 0;
+}
+
+int oracle_maxconv_points(const int64_t* x, const int64_t* y, int D, const uint64_t* ks,
+                          size_t nk, int64_t* out) {
+  if (D < 0 || D > 30) return 1;
+  for (size_t q = 0; q < nk; ++q) out[q] = maxconv_point(x, y, D, ks[q]);
   return 0;
 }
 

@@ -117,3 +117,24 @@ def test_maxconv_bench_workload(hc):
     plan = hc.maxconv_plan(D, vmax)
     assert plan["e"] == 4
     assert_equal(gpu_max(hc, x, y, vmax), oracle.maxconv_brute(x, y))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("D,vmax,e", [(17, 2, 3), (20, 1, 0)])
+def test_maxconv_largest_embeddings(hc, D, vmax, e):
+    """The largest convolutions the limb embedding reaches at these bounds:
+    D + e = 20 axes (a 28 GB int64 convolution in the workspace), sampled
+    outputs against the oracle's definition one output at a time, plus the
+    outputs with every digit equal."""
+    x, y = inputs.uniform_int_pair(D, 0, vmax, seed=500 + D)
+    assert hc.maxconv_plan(D, vmax)["e"] == e
+    z = hc.maxconv(T(x), T(y), vmax)
+    torch.cuda.synchronize()
+    n3 = 3 ** D
+    ks = np.unique(np.concatenate([
+        np.random.default_rng(D).integers(0, n3, size=20000),
+        [0, (n3 - 1) // 2, n3 - 1]]))
+    got = z[torch.from_numpy(ks.astype(np.int64)).to(DEV)].cpu().numpy()
+    assert_equal(got, oracle.maxconv_points(x, y, ks))
+    del z
+    torch.cuda.empty_cache()

@@ -184,3 +184,11 @@ def test_limb_embedding_catches_a_carry(oracle):
     W = oracle.convolve(limbs(x), limbs(y)).reshape(3 ** e, 3 ** D)
     wrong = [sum(int(W[d, k]) << (d * b) for d in range(3 ** e)) for k in range(3 ** D)]
     assert wrong != exact
+
+
+@pytest.mark.parametrize("D,vmax", [(0, 7), (3, 3), (8, 5)])
+def test_maxconv_points_equal_brute(oracle, D, vmax):
+    """The one-output-at-a-time definition agrees with the pair loop."""
+    x, y = inputs.uniform_int_pair(D, 0, vmax, seed=70 + D)
+    ks = np.arange(3 ** D)
+    assert np.array_equal(oracle.maxconv_points(x, y, ks), oracle.maxconv_brute(x, y))
