@@ -124,21 +124,24 @@ __global__ void __launch_bounds__(256) group_tile_kernel(const GroupPtrs* __rest
 // The same group tiles (intermediate only) stored with bulk copies
 // (tile_loop_bulk), when every instance's intermediate array of the group is
 // a plain device allocation.
-template <class M, int C>
-__global__ void __launch_bounds__(256) group_tile_bulk_kernel(const GroupPtrs* __restrict__ tab,
-                                                              const typename M::In* __restrict__ X,
-                                                              const typename M::In* __restrict__ Y,
-                                                              long long per, long long ntiles) {
+// T44: the two four-axis groups of C = 8 binary32 tiles (TileStages44,
+// 128 threads).
+template <class M, int C, bool T44 = false>
+__global__ void __launch_bounds__(T44 ? 128 : 256) group_tile_bulk_kernel(
+    const GroupPtrs* __restrict__ tab, const typename M::In* __restrict__ X,
+    const typename M::In* __restrict__ Y, long long per, long long ntiles) {
   typedef typename M::In In;
   typedef typename M::W W;
   extern __shared__ __align__(16) unsigned char smem[];
-  tile_loop_bulk<M, C>(
-      [&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); },
-      [&](long long t) {
-        const long long i = t / per, local = t - i * per;
-        return reinterpret_cast<W*>(tab[i].w) + local * p3(C);
-      },
-      ntiles, smem);
+  auto src = [&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); };
+  auto dst = [&](long long t) {
+    const long long i = t / per, local = t - i * per;
+    return reinterpret_cast<W*>(tab[i].w) + local * p3(C);
+  };
+  if constexpr (T44)
+    tile_loop_bulk<M, C, decltype(src), decltype(dst), TileStages44<M>>(src, dst, ntiles, smem);
+  else
+    tile_loop_bulk<M, C>(src, dst, ntiles, smem);
 }
 
 // Interpolation of the a = K1 + K2 outer axes of every instance of a group,
@@ -391,10 +394,12 @@ static cudaError_t launch_group_tile_c(const GroupPtrs* tab, const typename M::I
   if constexpr (use_bulk_tiles<M, C, FINAL>()) {
     if (bulk) {
       const size_t smem = TileBulk<M, C>::bytes;
-      auto k = group_tile_bulk_kernel<M, C>;
+      constexpr bool t44 = use_tile44<M, C>();
+      constexpr int threads = t44 ? 128 : 256;
+      auto k = group_tile_bulk_kernel<M, C, t44>;
       cudaError_t e = prep_kernel(k, smem);
       if (e != cudaSuccess) return e;
-      k<<<grid_for(k, 256, smem, ntiles), 256, smem, st>>>(tab, X, Y, per, ntiles);
+      k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(tab, X, Y, per, ntiles);
       return cudaGetLastError();
     }
   }

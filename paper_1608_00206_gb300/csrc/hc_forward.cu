@@ -69,15 +69,20 @@ __global__ void __launch_bounds__(256) tile_conv_kernel(const typename M::In* __
 
 // K2 with bulk stores (tile_loop_bulk): intermediate tiles into a plain
 // device allocation.
-template <class M, int C>
-__global__ void __launch_bounds__(256) tile_conv_bulk_kernel(const typename M::In* __restrict__ X,
-                                                             const typename M::In* __restrict__ Y,
-                                                             typename M::W* __restrict__ out,
-                                                             long long ntiles, long long pitch) {
+// T44: the two four-axis groups of C = 8 binary32 tiles (TileStages44,
+// 128 threads).
+template <class M, int C, bool T44 = false>
+__global__ void __launch_bounds__(T44 ? 128 : 256) tile_conv_bulk_kernel(
+    const typename M::In* __restrict__ X, const typename M::In* __restrict__ Y,
+    typename M::W* __restrict__ out, long long ntiles, long long pitch) {
   typedef typename M::In In;
   extern __shared__ __align__(16) unsigned char smem[];
-  tile_loop_bulk<M, C>([&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); },
-                       [&](long long t) { return out + t * pitch; }, ntiles, smem);
+  auto src = [&](long long t, int op) -> const In* { return (op ? Y : X) + t * p2(C); };
+  auto dst = [&](long long t) { return out + t * pitch; };
+  if constexpr (T44)
+    tile_loop_bulk<M, C, decltype(src), decltype(dst), TileStages44<M>>(src, dst, ntiles, smem);
+  else
+    tile_loop_bulk<M, C>(src, dst, ntiles, smem);
 }
 
 // HC_FP32_FF: the binary32 inputs as float-float pairs (x, 0), written once
@@ -118,11 +123,13 @@ static cudaError_t launch_tile_c(const typename M::In* X, const typename M::In* 
   if constexpr (use_bulk_tiles<M, C, FINAL>()) {
     if (is_device_allocation(out)) {
       const size_t smem = TileBulk<M, C>::bytes;
-      auto k = tile_conv_bulk_kernel<M, C>;
+      constexpr bool t44 = use_tile44<M, C>();
+      constexpr int threads = t44 ? 128 : 256;
+      auto k = tile_conv_bulk_kernel<M, C, t44>;
       cudaError_t e = prep_kernel(k, smem);
       if (e != cudaSuccess) return e;
-      k<<<grid_for(k, 256, smem, ntiles), 256, smem, st>>>(X, Y, (typename M::W*)out, ntiles,
-                                                           pitch);
+      k<<<grid_for(k, threads, smem, ntiles), threads, smem, st>>>(X, Y, (typename M::W*)out,
+                                                                   ntiles, pitch);
       return cudaGetLastError();
     }
   }
