@@ -10,6 +10,8 @@ and marshals numpy arrays.  Functions and the passages they follow:
 
 * :func:`brute_force` -- Algorithm 1 (naive convolution), hypercube case.
 * :func:`points`      -- the definition (Introduction) evaluated at chosen outputs.
+* :func:`points_rec`  -- the Methods recurrence evaluated at chosen outputs,
+  with its own rounding (full-size float checks on sampled outputs).
 * :func:`carry_free`  -- the carry-free 1D convolution (Discussion), from its
   definition, for vectors of any length.
 * :func:`convolve`    -- the Methods recurrence (3-way split, base case D = 0;
@@ -87,6 +89,7 @@ def _lib():
             lib.oracle_adjoint.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_adjoint_brute.argtypes = [vp, vp, vp, vp, vp, i, i]
             lib.oracle_zabs.argtypes = [vp, vp, vp, i]
+            lib.oracle_points_rec.argtypes = [vp, vp, i, i, vp, sz, vp]
             lib.oracle_maxconv_brute.argtypes = [vp, vp, vp, i]
             lib.oracle_maxconv_points.argtypes = [vp, vp, i, vp, sz, vp]
             lib.oracle_max_threads.restype = i
@@ -144,6 +147,21 @@ def points(x, y, ks) -> np.ndarray:
     out = np.empty(ks.size, dtype=x.dtype)
     if _lib().oracle_points(_ptr(x), _ptr(y), D, code, _ptr(ks), ks.size, _ptr(out)):
         raise RuntimeError("oracle_points failed")
+    return out
+
+
+def points_rec(x, y, ks) -> np.ndarray:
+    """z[k] at chosen flat indices k as the Methods recurrence computes it,
+    with its rounding (the 2^{#ones(k)} entries that z[k] depends on, run
+    through the recurrence with every output digit 1); bitwise equal to
+    convolve(x, y)[ks] in every dtype.  OpenMP over the outputs."""
+    x, y, D, code = _prep(x, y)
+    ks = np.ascontiguousarray(ks, dtype=np.uint64).reshape(-1)
+    if ks.size and int(ks.max()) >= 3 ** D:
+        raise ValueError("output index out of range")
+    out = np.empty(ks.size, dtype=x.dtype)
+    if _lib().oracle_points_rec(_ptr(x), _ptr(y), D, code, _ptr(ks), ks.size, _ptr(out)):
+        raise RuntimeError("oracle_points_rec failed")
     return out
 
 

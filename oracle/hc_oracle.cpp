@@ -153,6 +153,56 @@ int64_t maxconv_point(const int64_t* x, const int64_t* y, int D, size_t k) {
   return best;
 }
 
+// One output of the Methods recurrence with the recurrence's own rounding.
+// On an axis whose digit of k is 0 (or 2) the recurrence only descends into
+// the first (second) halves of x and y, so z[k] depends on the 2^m entries
+// whose bits agree with k on those axes (m = number of digits 1); gathered
+// in axis order they form an m-axis problem whose output digits are all 1,
+// and the recurrence on it performs, element by element, the same
+// additions, products and subtractions as the full recurrence does for
+// z[k].  rec_ones is that recurrence (z1 = (t - z0) - z2 on every axis).
+template <class T>
+T rec_ones(const T* x, const T* y, int m, T* scratch) {
+  if (m == 0) return x[0] * y[0];
+  const size_t h = (size_t)1 << (m - 1);
+  T* xs = scratch;
+  T* ys = scratch + h;
+  for (size_t i = 0; i < h; ++i) {
+    xs[i] = x[i] + x[h + i];
+    ys[i] = y[i] + y[h + i];
+  }
+  const T t = rec_ones(xs, ys, m - 1, scratch + 2 * h);
+  const T z0 = rec_ones(x, y, m - 1, scratch + 2 * h);
+  const T z2 = rec_ones(x + h, y + h, m - 1, scratch + 2 * h);
+  return (t - z0) - z2;
+}
+
+template <class T>
+T point_rec(const T* x, const T* y, int D, size_t k, std::vector<T>& buf) {
+  int dig[64];
+  size_t kk = k;
+  for (int d = D - 1; d >= 0; --d) { dig[d] = (int)(kk % 3); kk /= 3; }
+  int ones[64], m = 0;
+  size_t base = 0;
+  for (int d = 0; d < D; ++d) {
+    const size_t bit = (size_t)1 << (D - 1 - d);
+    if (dig[d] == 2) base |= bit;
+    if (dig[d] == 1) ones[m++] = d;
+  }
+  const size_t n = (size_t)1 << m;
+  buf.assign(2 * n + 2 * n + 4, T(0));
+  T* xc = buf.data();
+  T* yc = xc + n;
+  for (size_t s = 0; s < n; ++s) {  // s's bits, most significant first, on the digit-1 axes
+    size_t i = base;
+    for (int q = 0; q < m; ++q)
+      if ((s >> (m - 1 - q)) & 1u) i |= (size_t)1 << (D - 1 - ones[q]);
+    xc[s] = x[i];
+    yc[s] = y[i];
+  }
+  return rec_ones(xc, yc, m, yc + n);
+}
+
 // ---------------------------------------------------------------------------
 // The Methods recurrence (3-way split), on fresh temporaries:
 //   z[0] = x[0]*y[0];  z[2] = x[1]*y[1];
@@ -683,6 +733,28 @@ int oracle_maxconv_points(const int64_t* x, const int64_t* y, int D, const uint6
   if (D < 0 || D > 30) return 1;
   for (size_t q = 0; q < nk; ++q) out[q] = maxconv_point(x, y, D, ks[q]);
   return 0;
+}
+
+int oracle_points_rec(const void* x, const void* y, int D, int dtype, const uint64_t* ks,
+                      size_t nk, void* out) {
+  if (D < 0 || D > 40) return 1;
+  int bad = 0;
+#pragma omp parallel
+  {
+    std::vector<u64> bu;
+    std::vector<double> bd;
+    std::vector<float> bf;
+#pragma omp for schedule(dynamic, 64)
+    for (long long q = 0; q < (long long)nk; ++q) {
+      switch (dtype) {
+        case 0: ((u64*)out)[q] = point_rec((const u64*)x, (const u64*)y, D, ks[q], bu); break;
+        case 1: ((double*)out)[q] = point_rec((const double*)x, (const double*)y, D, ks[q], bd); break;
+        case 2: ((float*)out)[q] = point_rec((const float*)x, (const float*)y, D, ks[q], bf); break;
+        default: bad = 1;
+      }
+    }
+  }
+  return bad;
 }
 
 int oracle_max_threads(void) { return omp_get_max_threads(); }

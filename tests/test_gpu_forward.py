@@ -500,6 +500,36 @@ def test_int64_full_size(hc, D, sched):
     del z
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("kind,D,dist", [("float32", 18, "u01"), ("float32", 18, "normal"),
+                                         ("float32", 19, "u01"), ("float32", 20, "u01"),
+                                         ("float64", 18, "u01")])
+def test_float_full_size_sampled(hc, kind, D, dist):
+    """Floating-point convolutions at full size with the tuned default
+    schedules (the benchmark's D = 18 float32 form and the forward of the
+    D = 18 differentiation form, the D = 19 and 20 float32 plans, D = 18
+    float64): 20 000 sampled outputs and the all-0 and all-2 outputs (and,
+    up to D = 18, the all-1 output, which takes the oracle 3^D products)
+    against the recurrence evaluated at those outputs (oracle.points_rec),
+    bit for bit."""
+    dt = np.float32 if kind == "float32" else np.float64
+    if dist == "u01":
+        x, y = inputs.uniform01_pair(D, seed=3000 + D, dtype=dt)
+    else:
+        x = inputs.normal(1 << D, 3100 + D, dt)
+        y = inputs.normal(1 << D, 3200 + D, dt)
+    z = hc.convolve(torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV))
+    torch.cuda.synchronize()
+    n3 = 3 ** D
+    special = [0, n3 - 1] + ([(n3 - 1) // 2] if D <= 18 else [])  # all-1: 3^D oracle products
+    ks = np.unique(np.concatenate([np.random.default_rng(D).integers(0, n3, size=20000),
+                                   special]))
+    got = z[torch.from_numpy(ks.astype(np.int64)).to(DEV)].cpu().numpy()
+    assert_bit_equal(got, oracle.points_rec(x, y, ks))
+    del z
+    torch.cuda.empty_cache()
+
+
 def test_d20_int64_separable_points(hc):
     D = 20
     a = inputs.separable_factors(D, 1, "int")

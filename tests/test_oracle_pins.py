@@ -569,3 +569,22 @@ def test_direct_top_within_forward_bound(oracle, D, mt):
     zh = oracle.convolve_direct_top(x, y, mt).astype(np.float64)
     za = oracle.zabs(x, y)
     assert np.all(np.abs(zh - z_exact) <= oracle.gamma(3 * D + 1, U32) * za)
+
+
+@pytest.mark.parametrize("D", [0, 1, 5, 9, 12])
+@pytest.mark.parametrize("dt", [np.int64, np.float64, np.float32])
+def test_points_rec_is_the_recurrence_at_each_output(oracle, D, dt):
+    """The recurrence at single outputs (only the entries each output depends
+    on, every digit 1) gives the full recurrence's bits, in every dtype."""
+    if dt == np.int64:
+        x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=40 + D)
+    else:
+        x, y = inputs.uniform01_pair(D, seed=40 + D, dtype=dt)
+        x = x - dt(0.5)
+    full = oracle.convolve(x, y)
+    ks = np.arange(3 ** D) if D <= 9 else np.random.default_rng(D).integers(0, 3 ** D, 4000)
+    got = oracle.points_rec(x, y, ks)
+    bits = np.uint64 if np.dtype(dt).itemsize == 8 else np.uint32
+    assert np.array_equal(got.view(bits), full[ks].view(bits))
+    if dt == np.int64:
+        assert np.array_equal(got, oracle.points(x, y, ks))
