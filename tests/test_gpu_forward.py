@@ -95,6 +95,21 @@ def test_mixed_bit_exact(hc, D):
     assert_bit_equal(gpu_conv(hc, x, y, mixed=True), oracle.convolve_mixed(x, y))
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("mixed", [True, "ff"])
+def test_float_float_forms_full_size(hc, mixed):
+    """The benchmark's D = 16 precision forms (float32 probability
+    hypercubes; binary32 evaluation and products with float-float
+    interpolation, and every value in float-float) with their tuned
+    schedules: every output bitwise the oracle's recurrence in the same
+    arithmetic."""
+    D = 16
+    x, y = inputs.prob_exponential_pair(D, seed=1000)
+    x, y = x.astype(np.float32), y.astype(np.float32)
+    want = oracle.convolve_mixed(x, y) if mixed is True else oracle.convolve_ff(x, y)
+    assert_bit_equal(gpu_conv(hc, x, y, mixed=mixed), want)
+
+
 @pytest.mark.parametrize("D", list(range(0, 14)))
 def test_ff_bit_exact(hc, D):
     """Every value in float-float (HC_FP32_FF): bitwise the oracle's
