@@ -536,14 +536,37 @@ def _time_steps(wl, steps, warmup, dist):
         # comes from one eager launch of the same batch after the timed
         # region, scaled to the timed steps (the step time itself is the
         # replays' own, measured above).
-        _lib.lib().hc_profile_enable(1)
-        if wl.name == "batched":
-            wl.batch.launch()
-        else:
-            wl.eager_step()
-        torch.cuda.synchronize()
-        _lib.lib().hc_profile_enable(0)
-        eager = _lib.profile_collect()
+        eager = None
+        if wl.name != "batched":
+            # a single convolution: capture it once more with the tracer's
+            # event pairs inside the graph and replay that graph once, so
+            # that each kernel's time is its own, without the host's launch
+            # gaps of an eager call (which dominate steps of tens of us)
+            try:
+                _lib.lib().hc_profile_enable(1)
+                g2 = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g2, capture_error_mode="thread_local"):
+                    wl.eager_step()
+                _lib.lib().hc_profile_enable(0)
+                g2.replay()
+                torch.cuda.synchronize()
+                eager = _lib.profile_collect()
+                del g2
+                if not eager or min(v[1] for v in eager.values()) <= 0.0:
+                    eager = None  # no event timings from the replay: use an eager call
+            except Exception:  # capture refused: fall back to one eager call
+                _lib.lib().hc_profile_enable(0)
+                _lib.profile_collect()
+                eager = None
+        if eager is None:
+            _lib.lib().hc_profile_enable(1)
+            if wl.name == "batched":
+                wl.batch.launch()
+            else:
+                wl.eager_step()
+            torch.cuda.synchronize()
+            _lib.lib().hc_profile_enable(0)
+            eager = _lib.profile_collect()
         prof = {k: (v[0] * steps, v[1] * steps) for k, v in eager.items()}
     ms = _max_over_ranks(ms, dist, wl.dev)
     torch.cuda.synchronize()
@@ -915,6 +938,10 @@ def _measure(wl, steps, warmup, dist, world):
 # D = 14..19 of the D = 20 int64 workload (same value distribution, tuned
 # schedules): steps per D so that each point takes a fraction of a second.
 SWEEP_STEPS = {14: 200, 15: 100, 16: 60, 17: 40, 18: 30, 19: 20}
+# Sweep points up to this D replay their convolution from a CUDA graph (one
+# launch per step), so that the host's per-call work does not leave the GPU
+# idle inside the timed steps.
+SWEEP_GRAPH_MAX_D = 16
 # The training-system forms beside the plain method, each timed after the
 # headline: (workload, steps).
 FORMS = (("batched", 20), ("fwdbwd", 30), ("d16_fp64", 30), ("d16_mixed", 50),
@@ -944,8 +971,11 @@ def _sweep(dev, main_res, main_D, warmup):
         if D == main_D:
             continue
         wl = Workload("d20_int64", dev, 0, D)
+        if D <= SWEEP_GRAPH_MAX_D:
+            wl.use_graph()  # steps of a few launches and < 0.4 ms: replay one graph
         res = _measure(wl, SWEEP_STEPS[D], warmup, None, 1)
-        out[str(D)] = {"outputs": 3 ** D, **_brief(res)}
+        out[str(D)] = {"outputs": 3 ** D, **_brief(res),
+                       **({"cuda_graph": True} if wl.graph is not None else {})}
         del wl
         torch.cuda.empty_cache()
     out[str(main_D)] = {"outputs": 3 ** main_D, **_brief(main_res)}
@@ -1063,8 +1093,10 @@ def main():
                    "outputs_per_step": wl.outputs, "parallelism": f"replicas{world}",
                    **({"fused_max_d": wl.batch.fused_max_d} if args.workload == "batched" else {}),
                    **({"cuda_graph": True,
-                       "kernel_times": "per-kernel split from one eager launch after the "
-                                       "timed graph replays, scaled by steps"}
+                       "kernel_times": "per-kernel split from one replay of the step "
+                                       "captured with the tracer's event pairs (batched: one "
+                                       "eager launch) after the timed graph replays, scaled by "
+                                       "steps"}
                       if args.workload == "batched" or wl.graph is not None else {}),
                    "l2": "working set larger than L2 (129 MB); no flush"
                    if wl.alg_bytes >= L2_BYTES else
