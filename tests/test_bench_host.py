@@ -122,3 +122,18 @@ def test_float_float_slab_operation_count():
         tile = 2 * (3 ** 8 - 2 ** 8) * ea + 3 ** 8 * mu
         assert bound == "alu32"
         assert ops == 9 * (3 ** 6 * tile + 14 * 3 ** 13 * 22)
+
+
+def test_maxconv_kernel_bytes():
+    """The max-convolution's own kernels: the root reads the (D + e)-axis
+    convolution once and writes the 3^D maxima; the spread reads x, y and
+    writes the two limb cubes; the convolution's kernels are counted on its
+    D + e axes."""
+    wl = bench.Workload.__new__(bench.Workload)
+    wl.name, wl.D, wl.conv_D, wl.sched = "maxconv", 14, 18, {}
+    b, bound = bench.Workload.kernel_alg(wl, "maxconv_root", 1)
+    assert bound == "hbm" and b == 8 * (3 ** 18 + 3 ** 14)
+    b, _ = bench.Workload.kernel_alg(wl, "maxconv_spread", 1)
+    assert b == 8 * (2 * 2 ** 14 + 2 * 2 ** 18)
+    b, _ = bench.Workload.kernel_alg(wl, "interp_pass", 2)
+    assert b == 2 * 3 ** 18 * 8
