@@ -56,6 +56,16 @@ def test_int64_bit_exact(hc, D):
     assert_bit_equal(gpu_conv(hc, x, y), want)
 
 
+@pytest.mark.parametrize("D", [13, 14, 15, 16])
+def test_int64_sweep_sizes_bit_exact(hc, D):
+    """The benchmark sweep's smaller points with their tuned schedules (the
+    hybrid direct form on two top axes at D = 13, 15 and 16, whole-array
+    passes at 14; values in [-1000, 1000] as the D = 20 workload): every
+    output bitwise the oracle's recurrence."""
+    x, y = inputs.uniform_int_pair(D, -1000, 1000, seed=4000 + D)
+    assert_bit_equal(gpu_conv(hc, x, y), oracle.convolve(x, y, threads=16))
+
+
 @pytest.mark.parametrize("c", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("kmax", [1, 3, 4, 6])
 def test_int64_every_schedule(hc, c, kmax):
